@@ -1,0 +1,141 @@
+"""Pins of the oracle's stochastic-TDH engine (Sec. II.B, Eqs. 10-15) on tiny grids (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle import rpa, tdh
+from conftest import rel_err
+
+
+def _det_coeff(n_occ):
+    # deterministic TDH: L = N_occ stochastic orbitals with c = sqrt(N_occ) I gives eta_s = phi_s
+    return np.sqrt(n_occ) * np.eye(n_occ)
+
+
+@pytest.mark.parametrize("feedback", [False, True])
+def test_deterministic_tdh_converges_to_casida_at_second_order(tiny8, feedback):
+    """TDH of the full occupied set == the linear-response (Casida) damped W^pol up to O(dt^2)."""
+    p, v, e, phi = tiny8
+    g = tdh.Grid(p.N, p.box)
+    n_occ = 2
+    rho = phi[0] * phi[1]
+    errs = []
+    for dt in (0.04, 0.02):
+        pr = tdh.TDHParams(n_steps=int(round(4.0 / dt)), dt=dt, gamma=0.5, alpha=1e-6,
+                           clean_every=0, feedback=feedback)
+        w = tdh.tdh_w_pol(g, v, phi[:n_occ], rho, _det_coeff(n_occ), pr)
+        t = np.arange(pr.n_steps + 1) * dt
+        wc = rpa.casida_w_pol(g, e, phi, n_occ, rho, t, tdh.time_weights(pr), feedback=feedback)
+        errs.append(rel_err(w, wc))
+    assert errs[1] < 2e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5  # second order in dt
+
+
+def test_cleaning_is_second_order_for_the_full_set(tiny8):
+    """For the full occupied set the occupied-occupied components cancel in the density (Sec. II.B),
+    so Eq. (15) changes the deterministic W^pol only at O(alpha)."""
+    p, v, e, phi = tiny8
+    g = tdh.Grid(p.N, p.box)
+    rho = phi[0] * phi[1]
+    base = dict(n_steps=100, dt=0.04, gamma=0.5, alpha=1e-5)
+    w0 = tdh.tdh_w_pol(g, v, phi[:2], rho, _det_coeff(2), tdh.TDHParams(clean_every=0, **base))
+    w1 = tdh.tdh_w_pol(g, v, phi[:2], rho, _det_coeff(2), tdh.TDHParams(clean_every=10, **base))
+    assert rel_err(w1, w0) < 1e-4
+
+
+def test_single_occupied_state_stochastic_equals_deterministic(tiny8):
+    """With N_occ = 1 and random signs, n = 2 sum_l |eta_l|^2 = 2 |phi_1|^2 for any L (Eq. 14):
+    the stochastic W^pol equals the deterministic one to rounding."""
+    p, v, e, phi = tiny8
+    g = tdh.Grid(p.N, p.box)
+    rho = phi[0] * phi[0]
+    pr = tdh.TDHParams(n_steps=60, dt=0.05, gamma=0.3, alpha=1e-4, clean_every=10)
+    c = tdh.stochastic_coefficients(11, 10, 1, "sign")
+    w_st = tdh.tdh_w_pol(g, v, phi[:1], rho, c, pr)
+    w_det = tdh.tdh_w_pol(g, v, phi[:1], rho, np.ones((1, 1)), pr)
+    assert rel_err(w_st, w_det) < 1e-11
+
+
+def test_difference_form_equals_two_set_form(tiny16):
+    """The difference-form engine equals the paper's literal propagation of eta^alpha and eta^0."""
+    s = tiny16
+    g = tdh.Grid(s.N, s.box)
+    rho = s.phi[2] * s.phi[3]
+    c = tdh.stochastic_coefficients(5, 4, 4, "gaussian")
+    pr = tdh.TDHParams(n_steps=40, dt=0.05, gamma=0.1, alpha=1e-4, clean_every=10)
+    w1 = tdh.tdh_w_pol(g, s.v_loc, s.phi[:4], rho, c, pr)
+    w2 = tdh.tdh_w_pol_two_set(g, s.v_loc, s.phi[:4], rho, c, pr)
+    assert rel_err(w1, w2) < 1e-8
+
+
+def test_norm_conservation_and_renormalisation(tiny16):
+    s = tiny16
+    g = tdh.Grid(s.N, s.box)
+    prop = tdh._Propagator(g, s.v_loc, 0.05)
+    c = tdh.stochastic_coefficients(3, 4, 4, "gaussian")
+    a = tdh.stochastic_orbitals(c, s.phi[:4]).astype(complex)
+    q = tdh.coulomb_periodic(s.phi[2] * s.phi[3], g)
+    d = (np.exp(-1e-2j * q) - 1.0)[None] * a
+    n0 = np.real(g.inner(a, a))
+    u = 0.01 * q
+    for _ in range(20):  # unitary split-operator steps: |eta^alpha| conserved
+        a, d = prop.half_phase_pair(a, d, u)
+        a, d = prop.kinetic(a), prop.kinetic(d)
+        a, d = prop.half_phase_pair(a, d, u)
+    assert rel_err(np.real(g.inner(a + d, a + d)), n0) < 1e-13
+    d2 = tdh.clean(a, d, s.phi[:4], n0, g)
+    assert rel_err(np.real(g.inner(a + d2, a + d2)), n0) < 1e-13
+    # direct definition of Eq. (15) + renormalisation: eta^alpha <- c (eta0 + Q d) with
+    # c = sqrt(N0 / |eta0 + Q d|^2), i.e. d <- c Q d + (c - 1) eta0
+    ov = np.einsum("lzyx,szyx->ls", d, s.phi[:4]) * g.dV
+    assert np.max(np.abs(ov)) > 1e-6  # the propagated difference is contaminated
+    qd = d - np.einsum("ls,szyx->lzyx", ov, s.phi[:4])
+    cc = np.sqrt(n0 / np.real(g.inner(a + qd, a + qd)))[:, None, None, None]
+    assert rel_err(d2, cc * qd + (cc - 1.0) * a) < 1e-10
+
+
+def test_kick_leaves_density_unchanged_and_response_is_linear(tiny16):
+    s = tiny16
+    g = tdh.Grid(s.N, s.box)
+    rho = s.phi[2] * s.phi[3]
+    c = tdh.stochastic_coefficients(9, 6, 4, "gaussian")
+    rec = []
+    pr = tdh.TDHParams(n_steps=30, dt=0.05, gamma=0.1, alpha=1e-4, clean_every=10)
+    w1 = tdh.tdh_w_pol(g, s.v_loc, s.phi[:4], rho, c, pr, record=rec)
+    u0 = rec[0][1]
+    u_mid = np.max(np.abs(rec[15][1]))
+    assert np.max(np.abs(u0)) < 1e-3 * u_mid  # u(0) = O(alpha^2), u(t > 0) = O(alpha)
+    pr2 = tdh.TDHParams(n_steps=30, dt=0.05, gamma=0.1, alpha=0.5e-4, clean_every=10)
+    w2 = tdh.tdh_w_pol(g, s.v_loc, s.phi[:4], rho, c, pr2)
+    d12 = rel_err(w2, w1)
+    pr4 = tdh.TDHParams(n_steps=30, dt=0.05, gamma=0.1, alpha=0.25e-4, clean_every=10)
+    w4 = tdh.tdh_w_pol(g, s.v_loc, s.phi[:4], rho, c, pr4)
+    assert d12 < 1e-3
+    assert 1.6 < d12 / rel_err(w4, w2) < 2.4  # W^pol(alpha) - W^pol(alpha/2) = O(alpha)
+
+
+def test_stochastic_estimate_unbiased_and_converges_as_inverse_sqrt(tiny8):
+    """Without Hartree feedback the stochastic density response is bilinear in eta_l, so
+    E[W^pol] = deterministic W^pol (E[c c'] = delta) and the RMS error falls as N_s^-1/2."""
+    import sbse_inputs as si
+    p = si.model_system.Preset("t8b", N=8, box=8.0, n_wells=6, seed=4, n_occ=6, n_o=2, n_c=2)
+    v, e, phi = si.dense_eigensystem(p)
+    g = tdh.Grid(8, 8.0)
+    n_occ = 6
+    rho = phi[4] * phi[5]
+    pr = tdh.TDHParams(n_steps=40, dt=0.05, gamma=0.3, alpha=1e-5, clean_every=0,
+                       feedback=False)
+    w_det = tdh.tdh_w_pol(g, v, phi[:n_occ], rho, _det_coeff(n_occ), pr)
+    rms = {}
+    for n_s in (2, 8, 32):
+        errs = []
+        mean = np.zeros_like(w_det)
+        for seed in range(24):
+            c = tdh.stochastic_coefficients(1000 + seed, n_s, n_occ, "gaussian")
+            w = tdh.tdh_w_pol(g, v, phi[:n_occ], rho, c, pr)
+            mean += w / 24
+            errs.append(np.sum((w - w_det) ** 2))
+        rms[n_s] = np.sqrt(np.mean(errs))
+        # the seed mean is closer to the deterministic value than a single estimate by ~sqrt(24)
+        assert np.sqrt(np.sum((mean - w_det) ** 2)) < 0.45 * rms[n_s]
+    slope = np.polyfit(np.log([2, 8, 32]), np.log([rms[2], rms[8], rms[32]]), 1)[0]
+    assert -0.65 < slope < -0.35
