@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the stochastic-BSE hot path on GB300.
+
+One step = the whole hot path over one synthetic system: W_ij for all n_o(n_o+1)/2 occupied pairs
+by stochastic TDH (L = 10 stochastic orbitals, all time steps, cleaning, damped time integral),
+the exchange and direct contractions, the FP64 Tamm-Dancoff matrix A and its lowest excitons.
+Default workload: 48^3 grid (16 bohr box, 40 Gaussian wells, seed 1), N_occ = 60 (120 electrons),
+n_o = 8, n_c = 16 (36 pairs, A is 128 x 128), 1000 steps of dt = 0.05, gamma = 0.1, M = 10.
+
+Metric: W-applications per second (pairs completed per second of device time) for the whole job.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--precision fp64]
+Under torchrun every rank runs its own replica of the workload with its own stochastic seed
+(independent problems, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mid48")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n-steps", type=int, default=None, help="override the TDH step count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# the oracle as the CPU baseline / reference arm (runs in a single-threaded child process)
+
+def _oracle_child(spec_path: str) -> None:
+    import numpy as np
+
+    from oracle import tdh
+    with open(spec_path) as f:
+        spec = json.load(f)
+    z = np.load(spec["system"])
+    phi, v = z["phi"], z["v_loc"]
+    N, box, n_occ, n_o = spec["N"], spec["box"], spec["n_occ"], spec["n_o"]
+    g = tdh.Grid(N, box)
+    coeff = tdh.stochastic_coefficients(spec["seed"], spec["n_s"], n_occ, "gaussian")
+    op = tdh.TDHParams(n_steps=spec["sample_steps"], dt=spec["dt"], gamma=spec["gamma"],
+                       alpha=spec["alpha"], clean_every=spec["clean_every"])
+    phi_o = phi[n_occ - n_o:n_occ]
+    i, j = n_o - 2, n_o - 1
+    rho = phi_o[i] * phi_o[j]
+    times = []
+    for _ in range(spec["repeats"]):
+        t0 = time.perf_counter()
+        tdh.coulomb_periodic(rho, g) + tdh.tdh_w_pol(g, v, phi[:n_occ], rho, coeff, op)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"times": times}))
+
+
+def run_oracle_sample(system, preset, n_steps, sample_steps, repeats, seed):
+    """Time the oracle on one pair for `sample_steps` TDH steps, single-threaded, in a child."""
+    import numpy as np
+    with tempfile.TemporaryDirectory() as td:
+        sp = os.path.join(td, "sys.npz")
+        np.savez(sp, phi=system.phi[:preset.n_occ], v_loc=system.v_loc)
+        spec = dict(system=sp, N=system.N, box=system.box, n_occ=preset.n_occ, n_o=preset.n_o,
+                    n_s=preset.n_s, dt=preset.dt, gamma=preset.gamma, alpha=preset.alpha,
+                    clean_every=preset.clean_every, sample_steps=sample_steps, repeats=repeats,
+                    seed=seed)
+        jp = os.path.join(td, "spec.json")
+        with open(jp, "w") as f:
+            json.dump(spec, f)
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", jp],
+                           capture_output=True, text=True, env=env, cwd=ROOT)
+        if r.returncode != 0:
+            raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
+        times = json.loads(r.stdout.strip().splitlines()[-1])["times"]
+    # W-applications per second: one pair needs n_steps / sample_steps samples of this length
+    per_w = [t * n_steps / sample_steps for t in times]
+    return times, per_w
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.f.read().splitlines():
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def launch_count(P, L, n_steps, M, n, precision_mixed, n_exc):
+    """Kernels the library launches for one step of this benchmark (see the library sources)."""
+    k = 2 + 5 + 1 + 15 * n_steps + P
+    if M > 0:
+        cleans = [s for s in range(n_steps) if s % M == 0]
+        k += sum(11 + (1 if s > 0 else 0) for s in cleans)
+    k += 7 + (1 if precision_mixed else 0) + 2 + 1  # exchange, direct, assemble
+    k += 2 if n >= 3 else 1  # tridiagonalisation + bisection
+    return k
+
+
+def main():
+    args = parse()
+    if args.oracle_child:
+        _oracle_child(args.oracle_child)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import numpy as np
+
+    import sbse_inputs as si
+    pre = si.preset(args.workload)
+    n_steps = args.n_steps or pre.n_steps
+    P = pre.n_pairs
+    workload = (f"{pre.name}: {pre.N}^3 grid, box {pre.box} bohr, {pre.n_wells} Gaussian wells "
+                f"(seed {pre.seed}), N_occ={pre.n_occ} ({2 * pre.n_occ} electrons), n_o={pre.n_o}, "
+                f"n_c={pre.n_c}, {P} pairs, L={pre.n_s}, {n_steps} steps dt={pre.dt}, "
+                f"gamma={pre.gamma}, M={pre.clean_every}, A {pre.n_o * pre.n_c}^2, "
+                f"{pre.n_exc} excitons")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        system = si.make_system(pre)
+        sample = 20
+        times, per_w = run_oracle_sample(system, pre, n_steps, sample, args.warmup + args.steps,
+                                         seed=pre.seed)
+        timed = per_w[args.warmup:]
+        val = 1.0 / statistics.mean(timed)
+        line = {
+            "impl": "reference", "metric": "W-rho applications/sec (stochastic TDH, all pairs) + A build",
+            "value": val, "unit": "W-applications/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times[args.warmup:]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload, "precision": "fp64 oracle"},
+            "cpu_baseline": {"value": val, "unit": "W-applications/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one pair x {sample} TDH steps per step, scaled to "
+                                       f"{n_steps} steps; host {cpu_model()}"},
+            "e2e": {"value": val, "unit": "W-applications/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
+
+    system = si.make_system(pre)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = 20
+        times, per_w = run_oracle_sample(system, pre, n_steps, sample, 2, seed=pre.seed)
+        cpu = {"value": 1.0 / min(per_w), "unit": "W-applications/s", "cores": 1, "kind": "oracle",
+               "sample": f"one pair of {pre.name} x {sample} TDH steps (best of 2, "
+                         f"{min(times):.1f} s), scaled to {n_steps} steps; host {cpu_model()}"}
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2205_06690_gb300 import binding as B
+
+    pairs = [(i, j) for i in range(pre.n_o) for j in range(i, pre.n_o)]
+    prec = B.SBSE_MIXED if args.precision == "mixed" else B.SBSE_FP64
+    prm = B.TDHParams(n_s=pre.n_s, n_steps=n_steps, clean_every=pre.clean_every, dt=pre.dt,
+                      gamma=pre.gamma, alpha=pre.alpha, seed=pre.seed + 1000 * rank)
+    n = pre.n_o * pre.n_c
+    ns = pre.n_occ + pre.n_c
+    phi = np.ascontiguousarray(system.phi[:ns])
+    eps = np.ascontiguousarray(system.eps[:ns])
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    ctx = B.Context(local, prec)
+    ctx.set_grid(pre.N, pre.box, system.v_loc)
+    ctx.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi, eps, pre.scissor)
+    ext = torch.cuda.ExternalStream(B.sbse_get_stream(ctx.h), device=dev)
+
+    def step():
+        ctx.apply_W(prm, pairs)
+        ctx.build_A(copy_out=False)
+        return ctx.spectrum(pre.n_exc)
+
+    for _ in range(args.warmup):
+        ev = step()
+    # timed region: inputs resident in HBM; the propagated orbitals (P L n_g complex) exceed L2
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    B.sbse_profile(ctx.h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ext)
+    for _ in range(args.steps):
+        ev = step()
+    e1.record(ext)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    phase = {ph: B.sbse_phase_time(ctx.h, ph) for ph in range(5)}
+    B.sbse_profile(ctx.h, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * P / (ms_step / 1e3)
+
+    # A-build time (orbitals resident -> A in FP64), measured separately
+    ta0 = torch.cuda.Event(enable_timing=True)
+    ta1 = torch.cuda.Event(enable_timing=True)
+    ta0.record(ext)
+    ctx.build_A(copy_out=False)
+    ta1.record(ext)
+    torch.cuda.synchronize()
+    a_build_ms = ta0.elapsed_time(ta1)
+
+    # end to end through the C ABI: pinned host inputs -> excitons on the host, every step
+    e2e_steps = args.e2e_steps or max(1, min(args.steps, 2))
+    v_pin = torch.from_numpy(np.ascontiguousarray(system.v_loc)).pin_memory()
+    phi_pin = torch.from_numpy(phi).pin_memory()
+    eps_pin = torch.from_numpy(eps).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_grid(pre.N, pre.box, v_pin.numpy())
+        ctx.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi_pin.numpy(), eps_pin.numpy(), pre.scissor)
+        ev_e2e = step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = system.v_loc.nbytes + phi.nbytes + eps.nbytes + pre.n_s * pre.n_occ * 8
+    d2h = pre.n_exc * 8
+
+    # roofline of the dominant kernel group: one propagation step of all P*L + L orbitals
+    # (x pass with the potential phase, y, z with the kinetic phase, y, x with the density)
+    peak, src = measured_peaks()
+    csize = 8 if prec == B.SBSE_MIXED else 16
+    alg_bytes = (P * pre.n_s + pre.n_s) * pre.N ** 3 * 2 * csize
+    ms0, n0 = phase[0]
+    achieved = alg_bytes / (ms0 / n0 / 1e3) / 1e9 if n0 else None
+    dominant_share = ms0 / ms if ms else None
+    line = {
+        "metric": "W-rho applications/sec (stochastic TDH, all pairs) + A build",
+        "value": value, "unit": "W-applications/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == B.SBSE_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": workload,
+                   "precision": "mixed: FP32 FFT/propagation/cleaning, FP64 W accumulator, A, "
+                                "eigensolve" if prec == B.SBSE_MIXED else "fp64",
+                   "l2": "inputs larger than L2 (propagated orbitals "
+                         f"{P * pre.n_s * pre.N ** 3 * csize / 1e6:.0f} MB)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks,
+        "e2e": {"value": world * P / e2e_s, "unit": "W-applications/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * launch_count(P, pre.n_s, n_steps, pre.clean_every, n,
+                                                  prec == B.SBSE_MIXED, pre.n_exc),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "propagation step (5 FFT-pass kernels over all orbitals)",
+                     "peak_source": src, "share_of_step": dominant_share},
+        "a_build_ms": a_build_ms,
+        "phase_ms_per_step": {str(k): v[0] / args.steps for k, v in phase.items()},
+        "excitons_ha": [float(x) for x in ev],
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

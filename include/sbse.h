@@ -1,0 +1,169 @@
+/*
+ * sbse.h - C ABI of the GB300 library for the stochastic Bethe-Salpeter hot path of
+ * Bradbury, Nguyen, Caram & Neuhauser, "Bethe Salpeter Equation Spectra for Very Large Systems"
+ * (arXiv 2205.06690):
+ *
+ *   the action of the screened interaction W on occupied pair densities phi_i phi_j, computed by
+ *   stochastic time-dependent-Hartree (TDH) propagation (Sec. II.B, Eqs. 10-15); the
+ *   contraction of the screened potentials into the Tamm-Dancoff matrix A of Eq. (1); and the
+ *   lowest eigenvalues (excitons) of A.
+ *
+ * Conventions for every function:
+ *  - Returns SBSE_OK (0) or a negative SBSE_ERR_* code; sbse_last_error() gives the message.
+ *    No exception crosses the ABI. A failed call leaves the context usable unless it returned
+ *    SBSE_ERR_CUDA or SBSE_ERR_DEVICE_TIMEOUT, after which the context should be destroyed.
+ *  - Host buffers belong to the caller. Inputs are copied; nothing is retained after return.
+ *  - Calls are synchronous: on return all device work of the call has finished.
+ *  - One context per host thread. A context owns its device memory and one CUDA stream.
+ *  - Call order: sbse_set_grid -> sbse_set_orbitals -> sbse_apply_W (all pairs) ->
+ *    sbse_build_A -> sbse_spectrum. Out-of-order calls return SBSE_ERR_NOT_READY.
+ *  - Grid layout: a field on the N^3 periodic grid of the cubic box [0, L)^3 is N^3 doubles,
+ *    point r = h (ix, iy, iz), h = L/N, index ix + N (iy + N iz) (x fastest).
+ *  - Units: Hartree atomic units (bohr, Hartree, hbar = 1).
+ */
+#ifndef SBSE_H
+#define SBSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SBSE_OK 0
+#define SBSE_ERR_INVALID_ARG (-1)   /* NULL pointer, value out of range */
+#define SBSE_ERR_SHAPE (-2)         /* unsupported grid size or window sizes */
+#define SBSE_ERR_OOM (-3)           /* device allocation failed */
+#define SBSE_ERR_DEVICE_TIMEOUT (-4)/* a bounded device-side wait gave up */
+#define SBSE_ERR_NOT_READY (-5)     /* call order violated */
+#define SBSE_ERR_NUMERIC (-6)       /* NaN or Inf in an input or a result */
+#define SBSE_ERR_CUDA (-7)          /* CUDA runtime error */
+#define SBSE_ERR_UNSUPPORTED (-8)   /* option not implemented in this build */
+
+/* precision modes (sbse_create) */
+#define SBSE_FP64 0  /* every step in FP64 */
+#define SBSE_MIXED 1 /* FFTs, propagation, cleaning in FP32; W accumulator, A, eigensolve FP64 */
+
+/* distribution of the stochastic coefficients c[l][s] of Eq. (14) */
+#define SBSE_COEFF_GAUSSIAN 0 /* N(0, 1) */
+#define SBSE_COEFF_SIGN 1     /* +-1, as printed in Eq. (14) */
+
+/* terms of Eq. (1) included by sbse_build_A (the diagonal eps_a - eps_i + Delta is always in) */
+#define SBSE_EXCHANGE 1u /* + 2 (ia|jb) */
+#define SBSE_DIRECT 2u   /* - (phi_a phi_b | W | phi_i phi_j) */
+
+typedef struct sbse_ctx sbse_ctx;
+
+/* Parameters of one stochastic-TDH run (Sec. II.B; values used in Sec. III: L = 10,
+ * dt = 0.1, M = 10, gamma = 0.1 Ha).
+ *   n_s         L, number of stochastic occupied orbitals eta_l (Eq. 14), 1..64
+ *   n_steps     N_t, number of split-operator steps; W^pol integrates t in [0, N_t dt] (Eq. 13)
+ *   clean_every M of Eq. (15) (0 = never clean); cleaning happens before step n when n % M == 0
+ *   dt          time step (a.u.)
+ *   gamma       Gaussian damping width of Eq. (13) (Ha)
+ *   alpha       kick strength of psi_s(0) = exp(-i alpha q_ij) phi_s (paper: 1e-6 .. 1e-4)
+ *   seed        key of the counter-based splitmix64 stream for c[l][s] (see sbse_coefficients)
+ *   coeff_dist  SBSE_COEFF_GAUSSIAN or SBSE_COEFF_SIGN
+ *   feedback    1 = TDH (u enters the propagation, RPA screening); 0 = propagate with H0 only
+ *               (u is still recorded), which gives v chi0 v instead of v chi v */
+typedef struct {
+  int n_s;
+  int n_steps;
+  int clean_every;
+  double dt;
+  double gamma;
+  double alpha;
+  uint64_t seed;
+  int coeff_dist;
+  int feedback;
+} sbse_tdh_params;
+
+/* Create a context on CUDA device `device` with precision SBSE_FP64 or SBSE_MIXED.
+ * *out receives the context (NULL on failure). Errors: INVALID_ARG, CUDA. */
+int sbse_create(sbse_ctx **out, int device, int precision);
+
+/* Free all device memory and the stream of the context. NULL is allowed. */
+void sbse_destroy(sbse_ctx *ctx);
+
+/* Define the grid and the local potential V_loc of H0 = -1/2 Laplacian + V_loc.
+ * n: points per axis, with prime factors in {2, 3, 5}, 4 <= n <= 128.
+ * box: edge L of the cubic box (bohr, > 0).
+ * v_loc: host, n^3 doubles, x fastest; copied.
+ * The kinetic operator is spectral (plane waves of the periodic box), the Coulomb operator is
+ * the periodic 4 pi / |G|^2 with the G = 0 term removed (the paper's finite-box treatment,
+ * Sec. II.B). Resets orbitals and results. Errors: INVALID_ARG, SHAPE, OOM, NUMERIC, CUDA. */
+int sbse_set_grid(sbse_ctx *ctx, int n, double box, const double *v_loc);
+
+/* Set the orbitals of the closed-shell system (Sec. II, "Method": 2 N_occ electrons, n_o valence
+ * states phi_i and n_c conduction states phi_a, eigenstates of H0).
+ * phi: host, (n_occ + n_c) x n^3 doubles, states in ascending energy, real, normalised so that
+ *      sum_r phi_s(r)^2 h^3 = 1; rows 0..n_occ-1 are all occupied states.
+ * eps: host, n_occ + n_c eigenvalues (Ha).
+ * The valence window is the top n_o occupied states (i = 0..n_o-1 <-> state n_occ - n_o + i) and
+ * the conduction window the bottom n_c virtual states (a = 0..n_c-1 <-> state n_occ + a).
+ * scissor: Delta of Eq. (9), added to every eps_a - eps_i on the diagonal of A.
+ * Requires sbse_set_grid. Resets results. Errors: INVALID_ARG, NOT_READY, OOM, NUMERIC, CUDA. */
+int sbse_set_orbitals(sbse_ctx *ctx, int n_occ, int n_o, int n_c, const double *phi,
+                      const double *eps, double scissor);
+
+/* Host-only helper: the coefficient matrix c[l][s] (n_s x n_occ, row-major) that sbse_apply_W
+ * draws for `seed`. Output k of splitmix64 started from state `seed` is
+ * z = mix(seed + (k + 1) * 0x9E3779B97F4A7C15). SIGN: c = -1 if bit 63 of output l*n_occ + s is
+ * set, else +1. GAUSSIAN: u1, u2 = 53-bit uniforms (z >> 11) * 2^-53 of outputs 2(l*n_occ + s)
+ * and 2(l*n_occ + s) + 1; c = sqrt(-2 ln(1 - u1)) cos(2 pi u2). Errors: INVALID_ARG. */
+int sbse_coefficients(uint64_t seed, int n_s, int n_occ, int dist, double *out);
+
+/* Compute the screened potentials W_ij(r) = q_ij(r) + W^pol_ij(r) (Sec. II.B: q_ij = v phi_i phi_j,
+ * W^pol_ij from Eq. 13) for n_pairs pairs (pi[k], pj[k]) of valence-window indices,
+ * 0 <= pi[k] <= pj[k] < n_o, by stochastic TDH with the parameters p:
+ *   eta_l = L^-1/2 sum_{s <= N_occ} c[l][s] phi_s (Eq. 14); kick exp(-i alpha q_ij);
+ *   split-operator propagation of Eq. (10) with u_ij = v (n^alpha - n^0) (Eq. 11), both sets
+ *   propagated; cleaning (Eq. 15) plus renormalisation every M steps; damped trapezoid
+ *   integral of alpha^-1 u_ij (Eq. 13).
+ * coeff: optional host n_s x n_occ matrix c[l][s]; NULL draws it from p->seed, p->coeff_dist.
+ * w_out: optional host buffer n_pairs x n^3 doubles receiving W_ij; NULL keeps the results on
+ *        the device only. Results are always kept on the device for sbse_build_A.
+ * Requires sbse_set_orbitals. Errors: INVALID_ARG, NOT_READY, OOM, NUMERIC, CUDA. */
+int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int *pi,
+                 const int *pj, const double *coeff, double *w_out);
+
+/* Assemble the Tamm-Dancoff matrix of Eq. (1), in FP64:
+ *   A(ia, jb) = (eps_a - eps_i + Delta) delta_ij delta_ab + 2 (ia|jb) - (phi_a phi_b|W|phi_i phi_j)
+ * with (ia|jb) = sum_r phi_i phi_a (r) [v phi_j phi_b](r) h^3 (exchange element after Eq. 1) and
+ * (phi_a phi_b|W|phi_i phi_j) = sum_r phi_a phi_b (r) W_ij(r) h^3 (direct element), W_ji = W_ij.
+ * Index ia = i * n_c + a. terms: bitwise OR of SBSE_EXCHANGE and SBSE_DIRECT (0 gives the
+ * diagonal only). SBSE_DIRECT requires W for all n_o (n_o + 1) / 2 pairs.
+ * a_out: optional host (n_o n_c)^2 doubles, row-major; NULL keeps A on the device.
+ * Errors: INVALID_ARG, NOT_READY, OOM, CUDA. */
+int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out);
+
+/* Lowest k eigenvalues of A (Eq. 1; the exciton energies, Ha), ascending, by an FP64
+ * Householder tridiagonalisation and Sturm bisection on the device.
+ * evals: host, k doubles. evecs: must be NULL (eigenvectors are not provided by this build).
+ * Requires sbse_build_A. Errors: INVALID_ARG, NOT_READY, UNSUPPORTED, CUDA. */
+int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs);
+
+/* Message of the last failed call on ctx ("" if none). The pointer stays valid until the next
+ * call on ctx. ctx may be NULL (message of the last failed sbse_create on this thread). */
+const char *sbse_last_error(const sbse_ctx *ctx);
+
+/* The CUDA stream (cudaStream_t) all device work of ctx is issued on, for event timing by the
+ * caller. Errors: INVALID_ARG. */
+int sbse_get_stream(const sbse_ctx *ctx, void **stream);
+
+/* Per-phase device timing. When enabled, CUDA events bracket each phase launch group inside
+ * sbse_apply_W and sbse_build_A; sbse_phase_time reports the summed device milliseconds and the
+ * number of launches of one phase since the last reset (enable resets the counters).
+ * phase: 0 = orbital propagation step (phase + 3D FFT + kinetic + inverse FFT + induced density),
+ *        1 = Poisson solve and time-integral accumulation, 2 = cleaning, 3 = contractions (K, D),
+ *        4 = A assembly + eigensolve. Errors: INVALID_ARG, CUDA. */
+int sbse_profile(sbse_ctx *ctx, int enable);
+int sbse_phase_time(sbse_ctx *ctx, int phase, double *ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBSE_H */

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libsbse.so (C ABI in include/sbse.h), with the same function names.
+
+Only argument marshalling happens here: every step of the computation runs in the library's CUDA
+kernels. Importing works without a GPU; loading the library requires it to have been built
+(`paper_2205_06690_gb300.build.build()`), and there is no fallback if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsbse.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "sbse.h")
+
+SBSE_OK = 0
+SBSE_ERR_INVALID_ARG = -1
+SBSE_ERR_SHAPE = -2
+SBSE_ERR_OOM = -3
+SBSE_ERR_DEVICE_TIMEOUT = -4
+SBSE_ERR_NOT_READY = -5
+SBSE_ERR_NUMERIC = -6
+SBSE_ERR_CUDA = -7
+SBSE_ERR_UNSUPPORTED = -8
+SBSE_FP64 = 0
+SBSE_MIXED = 1
+SBSE_COEFF_GAUSSIAN = 0
+SBSE_COEFF_SIGN = 1
+SBSE_EXCHANGE = 1
+SBSE_DIRECT = 2
+
+_ERR_NAMES = {v: k for k, v in globals().items() if k.startswith("SBSE_ERR_")}
+
+
+class SbseError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sbse_tdh_params(C.Structure):
+    _fields_ = [("n_s", C.c_int), ("n_steps", C.c_int), ("clean_every", C.c_int),
+                ("dt", C.c_double), ("gamma", C.c_double), ("alpha", C.c_double),
+                ("seed", C.c_uint64), ("coeff_dist", C.c_int), ("feedback", C.c_int)]
+
+
+@dataclasses.dataclass
+class TDHParams:
+    n_s: int = 10
+    n_steps: int = 200
+    clean_every: int = 10
+    dt: float = 0.05
+    gamma: float = 0.1
+    alpha: float = 1e-4
+    seed: int = 0
+    coeff_dist: int = SBSE_COEFF_GAUSSIAN
+    feedback: int = 1
+
+    def to_c(self) -> sbse_tdh_params:
+        return sbse_tdh_params(self.n_s, self.n_steps, self.clean_every, self.dt, self.gamma,
+                               self.alpha, self.seed, self.coeff_dist, int(self.feedback))
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libsbse.so; raise if it has not been built (there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2205_06690_gb300.build")
+    lib = C.CDLL(LIB_PATH)
+    vp, i, d, dp, ip = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    sig = {
+        "sbse_create": (i, [C.POINTER(vp), i, i]),
+        "sbse_destroy": (None, [vp]),
+        "sbse_set_grid": (i, [vp, i, d, dp]),
+        "sbse_set_orbitals": (i, [vp, i, i, i, dp, dp, d]),
+        "sbse_coefficients": (i, [C.c_uint64, i, i, i, dp]),
+        "sbse_apply_W": (i, [vp, C.POINTER(sbse_tdh_params), i, ip, ip, dp, dp]),
+        "sbse_build_A": (i, [vp, C.c_uint, dp]),
+        "sbse_spectrum": (i, [vp, i, dp, dp]),
+        "sbse_last_error": (C.c_char_p, [vp]),
+        "sbse_get_stream": (i, [vp, C.POINTER(vp)]),
+        "sbse_profile": (i, [vp, i]),
+        "sbse_phase_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions declared in include/sbse.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(sbse_\w+)\s*\(", txt, re.M)))
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(ctx, rc):
+    if rc != SBSE_OK:
+        raise SbseError(rc, sbse_last_error(ctx))
+
+
+def sbse_last_error(ctx) -> str:
+    s = load().sbse_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def sbse_create(device: int = 0, precision: int = SBSE_FP64):
+    h = C.c_void_p()
+    _check(None, load().sbse_create(C.byref(h), device, precision))
+    return h
+
+
+def sbse_destroy(ctx) -> None:
+    load().sbse_destroy(ctx)
+
+
+def sbse_set_grid(ctx, n: int, box: float, v_loc) -> None:
+    v = _f64(v_loc)
+    if v.size != n ** 3:
+        raise ValueError("v_loc must have n^3 values")
+    _check(ctx, load().sbse_set_grid(ctx, n, box, _dptr(v)))
+
+
+def sbse_set_orbitals(ctx, n_occ: int, n_o: int, n_c: int, phi, eps, scissor: float) -> None:
+    ph, ep = _f64(phi), _f64(eps)
+    if ep.size < n_occ + n_c or ph.size % (n_occ + n_c) != 0:
+        raise ValueError("phi must be (n_occ + n_c) x n^3 and eps n_occ + n_c")
+    _check(ctx, load().sbse_set_orbitals(ctx, n_occ, n_o, n_c, _dptr(ph), _dptr(ep), scissor))
+
+
+def sbse_coefficients(seed: int, n_s: int, n_occ: int, dist: int = SBSE_COEFF_GAUSSIAN):
+    out = np.empty((n_s, n_occ))
+    rc = load().sbse_coefficients(C.c_uint64(seed), n_s, n_occ, dist, _dptr(out))
+    if rc != SBSE_OK:
+        raise SbseError(rc, "invalid arguments")
+    return out
+
+
+def sbse_apply_W(ctx, params: TDHParams, pairs, coeff=None, n_g: int | None = None):
+    """Run the stochastic TDH for `pairs` [(i, j), ...]; returns W (n_pairs x n_g) when n_g is given,
+    else keeps the results on the device and returns None."""
+    pi = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
+    pj = np.ascontiguousarray([p[1] for p in pairs], dtype=np.int32)
+    cf = None if coeff is None else _f64(coeff)
+    out = None if n_g is None else np.empty((len(pairs), n_g))
+    cp = params.to_c()
+    ip = C.POINTER(C.c_int)
+    _check(ctx, load().sbse_apply_W(ctx, C.byref(cp), len(pairs), pi.ctypes.data_as(ip),
+                                    pj.ctypes.data_as(ip), _dptr(cf), _dptr(out)))
+    return out
+
+
+def sbse_build_A(ctx, terms: int = SBSE_EXCHANGE | SBSE_DIRECT, n: int | None = None):
+    """Assemble A on the device; returns it (n x n) when n = n_o * n_c is given."""
+    out = None if n is None else np.empty((n, n))
+    _check(ctx, load().sbse_build_A(ctx, terms, _dptr(out)))
+    return out
+
+
+def sbse_spectrum(ctx, k: int):
+    ev = np.empty(k)
+    _check(ctx, load().sbse_spectrum(ctx, k, _dptr(ev), None))
+    return ev
+
+
+def sbse_get_stream(ctx) -> int:
+    s = C.c_void_p()
+    _check(ctx, load().sbse_get_stream(ctx, C.byref(s)))
+    return int(s.value or 0)
+
+
+def sbse_profile(ctx, enable: bool) -> None:
+    _check(ctx, load().sbse_profile(ctx, int(enable)))
+
+
+def sbse_phase_time(ctx, phase: int):
+    ms = C.c_double()
+    n = C.c_longlong()
+    _check(ctx, load().sbse_phase_time(ctx, phase, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+class Context:
+    """Owning wrapper: `with Context(device, precision) as c: c.set_grid(...)`."""
+
+    def __init__(self, device: int = 0, precision: int = SBSE_FP64):
+        self.h = sbse_create(device, precision)
+        self.n_g = None
+        self.n = None
+
+    def close(self):
+        if self.h:
+            sbse_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_grid(self, n, box, v_loc):
+        sbse_set_grid(self.h, n, box, v_loc)
+        self.n_g = n ** 3
+
+    def set_orbitals(self, n_occ, n_o, n_c, phi, eps, scissor):
+        sbse_set_orbitals(self.h, n_occ, n_o, n_c, phi, eps, scissor)
+        self.n = n_o * n_c
+
+    def apply_W(self, params, pairs, coeff=None, copy_out=False):
+        return sbse_apply_W(self.h, params, pairs, coeff, self.n_g if copy_out else None)
+
+    def build_A(self, terms=SBSE_EXCHANGE | SBSE_DIRECT, copy_out=True):
+        return sbse_build_A(self.h, terms, self.n if copy_out else None)
+
+    def spectrum(self, k):
+        return sbse_spectrum(self.h, k)

@@ -1,0 +1,91 @@
+// Host-side interface between the translation units of the sbse library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sbse {
+
+// Device tables of one grid, in working precision T.
+template <typename T> struct GridTables {
+  int N = 0;
+  long long ng = 0;
+  FftPlan plan{};
+  C2<T> *tw = nullptr;      // exp(-2 pi i k / N), k < N
+  C2<T> *kin = nullptr;     // exp(-i k_m^2 dt / 2) per axis index m (rebuilt per dt)
+  T *k2 = nullptr;          // k_m^2 per axis index m
+  T *v_loc = nullptr;       // V_loc(r), ng
+};
+
+// ---- FFT passes (tdh_kernels.cu). Items are contiguous arrays of ng complex values.
+enum XfwdMode { XF_PHASE_A = 0, XF_PHASE_PAIR = 1, XF_PACK_DN = 2, XF_PACK_PROD = 3 };
+
+template <typename T> struct XfwdArgs {
+  int mode;
+  int n_items;           // orbitals (A: L, PAIR: P*L) or Poisson slots
+  const C2<T> *in;       // A: a_cur; PAIR: d (in place)
+  C2<T> *out;            // A: a_next; PAIR: d; PACK: packed work buffer
+  const C2<T> *a;        // PAIR: a_cur
+  const T *u;            // PAIR: u per pair (ng each)
+  int L;                 // PAIR: orbitals per pair
+  T tau;                 // phase time: V, u multiplied by tau (dt or dt/2)
+  int feedback;          // PAIR: 0 -> u ignored
+  const T *dn;           // PACK_DN: density per pair; slot s packs 2s (re) and 2s+1 (im)
+  int n_dn;              // PACK_DN: number of densities
+  const T *orb;          // PACK_PROD: orbital rows (ng each)
+  const int4 *prod;      // PACK_PROD: per slot (i1, j1, i2, j2); i2 < 0 -> imaginary part 0
+};
+
+template <typename T> void launch_xfwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
+template <typename T> void launch_ypass(const GridTables<T> &g, C2<T> *data, int n_items, int sign,
+                                        cudaStream_t s);
+enum ZMult { Z_KINETIC = 0, Z_POISSON = 1 };
+template <typename T> void launch_zpass(const GridTables<T> &g, C2<T> *data, int n_items, int mult,
+                                        cudaStream_t s);
+// inverse x pass of orbitals; with dens != nullptr, items are grouped L per pair and the induced
+// density 2 sum_l (2 Re(conj(a_l) d_l) + |d_l|^2) of each pair is written to dens[pair].
+template <typename T> void launch_xinv_orb(const GridTables<T> &g, C2<T> *data, int n_items,
+                                           const C2<T> *a_next, int L, T *dens, cudaStream_t s);
+// inverse x pass of packed Poisson slots: potential of density 2s (re) / 2s+1 (im) ->
+// u_out[k] (if non-null) and acc[k] = acc[k] * keep + coef * value (if acc non-null), k < n_out.
+template <typename T> void launch_xinv_poisson(const GridTables<T> &g, C2<T> *data, int n_slots,
+                                               int n_out, T *u_out, double *acc, double coef,
+                                               double keep, cudaStream_t s);
+
+// ---- elementwise and reduction kernels (tdh_kernels.cu)
+template <typename T> void launch_init_a(const GridTables<T> &g, const double *phi, int n_occ,
+                                         const double *coeff, int L, C2<T> *a, double *part,
+                                         int *n_part, cudaStream_t s);
+void launch_reduce_cols(const double *part, int rows, int cols, double scale, double *out,
+                        cudaStream_t s);
+template <typename T> void launch_kick(const GridTables<T> &g, const double *q, int P, const C2<T> *a,
+                                       int L, double alpha, C2<T> *d, cudaStream_t s);
+template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const T *u,
+                                             int P, int L, T tau, int feedback, cudaStream_t s);
+template <typename T> void launch_density(const GridTables<T> &g, const C2<T> *a, const C2<T> *d,
+                                          int P, int L, T *dens, cudaStream_t s);
+// cleaning of Eq. (15): overlaps O[c][s] = dV sum_r phi_s d_c (c < P*L complex columns)
+template <typename T> void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
+                                        const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
+                                        double dV, double *work, size_t work_bytes, cudaStream_t s);
+template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L);
+// d64 -> T conversion and FP64 -> T copies
+template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s);
+int scan_nonfinite(const double *x, long long n, int *flag_dev, cudaStream_t s);
+
+// ---- contractions (contract.cu)
+// out[m][n] = scale * sum_r X_m(r) Y_n(r), X_m = F[xi[m].x](r) * F[xi[m].y](r), Y_n = Y[n] row
+template <typename T> void launch_prod_gemm(const T *F, const int2 *xi, int M, const T *Y, int Nn,
+                                            long long ng, double scale, double *out, double *work,
+                                            size_t work_bytes, cudaStream_t s);
+template <typename T> size_t prod_gemm_work_bytes(int M, int Nn, long long ng);
+void launch_assemble_A(const double *eps_o, const double *eps_c, int n_o, int n_c, double scissor,
+                       const double *K, const double *Dab, int P, double *A, cudaStream_t s);
+
+// ---- eigensolver (eig.cu)
+int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, cudaStream_t s);
+size_t eig_work_bytes(int n);
+
+}  // namespace sbse

@@ -1,0 +1,816 @@
+// C ABI of the sbse library (declared in include/sbse.h): context management, validation, the
+// host-side splitmix64 coefficient stream and the orchestration of the device kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "sbse.h"
+
+namespace sbse {
+void init_fft_kernels();
+}
+
+using namespace sbse;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+struct PhaseClock {
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
+  std::vector<int> phase;
+  size_t used = 0;
+};
+
+}  // namespace
+
+struct sbse_ctx {
+  int device = 0;
+  int precision = SBSE_FP64;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // grid
+  int N = 0;
+  double box = 0, h = 0, dV = 0;
+  long long ng = 0;
+  GridTables<float> g32;
+  GridTables<double> g64;
+  double *v64 = nullptr;
+  double kin_dt = -1.0;
+  // orbitals
+  int n_occ = 0, n_o = 0, n_c = 0, n_states = 0;
+  double scissor = 0;
+  double *phi64 = nullptr;
+  float *phi32 = nullptr;
+  std::vector<double> eps;
+  double *eps_dev = nullptr;  // eps_o (n_o) then eps_c (n_c)
+  // results
+  double *W = nullptr;  // P_all x ng, canonical pair order
+  std::vector<char> have;
+  double *A = nullptr;
+  bool have_A = false;
+  // scratch
+  DevBuf ws[16];
+  int *flag = nullptr;
+  // profiling
+  bool prof = false;
+  PhaseClock clk;
+};
+
+namespace {
+
+enum Ws {
+  WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG
+};
+
+int fail(sbse_ctx *c, int code, const std::string &msg) {
+  c->err = msg;
+  return code;
+}
+
+int cuda_fail(sbse_ctx *c, cudaError_t e, const char *where) {
+  c->err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  return SBSE_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+#define CHECK_LAUNCH(where)                                   \
+  do {                                                        \
+    cudaError_t e_ = cudaGetLastError();                      \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);  \
+  } while (0)
+
+template <typename X> int dalloc(sbse_ctx *ctx, X **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return SBSE_OK;
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, SBSE_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  return SBSE_OK;
+}
+
+template <typename X> void dfree(X *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+int ensure(sbse_ctx *ctx, int slot, size_t bytes, void **out) {
+  DevBuf &b = ctx->ws[slot];
+  if (b.cap < bytes) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    int rc = dalloc(ctx, &b.p, bytes);
+    if (rc) return rc;
+    b.cap = bytes;
+  }
+  *out = b.p;
+  return SBSE_OK;
+}
+
+void free_scratch(sbse_ctx *ctx) {
+  for (auto &b : ctx->ws) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+}
+
+void free_results(sbse_ctx *ctx) {
+  dfree(ctx->W);
+  dfree(ctx->A);
+  ctx->have.clear();
+  ctx->have_A = false;
+}
+
+void free_orbitals(sbse_ctx *ctx) {
+  dfree(ctx->phi64);
+  dfree(ctx->phi32);
+  dfree(ctx->eps_dev);
+  ctx->eps.clear();
+  ctx->n_occ = ctx->n_o = ctx->n_c = ctx->n_states = 0;
+  free_results(ctx);
+}
+
+template <typename T> void free_tables(GridTables<T> &g) {
+  dfree(g.tw);
+  dfree(g.kin);
+  dfree(g.k2);
+  dfree(g.v_loc);
+  g = GridTables<T>{};
+}
+
+void free_grid(sbse_ctx *ctx) {
+  free_orbitals(ctx);
+  free_tables(ctx->g32);
+  free_tables(ctx->g64);
+  dfree(ctx->v64);
+  ctx->N = 0;
+  ctx->ng = 0;
+  ctx->kin_dt = -1.0;
+}
+
+bool make_plan(int n, FftPlan *pl) {
+  pl->n = n;
+  pl->nst = 0;
+  int m = n;
+  while (m % 4 == 0 && pl->nst < kMaxStages) { pl->radix[pl->nst++] = 4; m /= 4; }
+  while (m % 2 == 0 && pl->nst < kMaxStages) { pl->radix[pl->nst++] = 2; m /= 2; }
+  while (m % 3 == 0 && pl->nst < kMaxStages) { pl->radix[pl->nst++] = 3; m /= 3; }
+  while (m % 5 == 0 && pl->nst < kMaxStages) { pl->radix[pl->nst++] = 5; m /= 5; }
+  return m == 1;
+}
+
+// angular wave number of FFT index m on an n-point axis of edge L (symmetric at Nyquist in k^2)
+double kval(int m, int n, double L) {
+  const int mm = (m <= (n - 1) / 2) ? m : m - n;
+  return 2.0 * M_PI / L * (double)mm;
+}
+
+template <typename T> int build_tables(sbse_ctx *ctx, GridTables<T> &g, const double *v_host) {
+  const int N = ctx->N;
+  g.N = N;
+  g.ng = ctx->ng;
+  make_plan(N, &g.plan);
+  std::vector<C2<T>> tw(N);
+  std::vector<T> k2(N);
+  for (int k = 0; k < N; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)N;
+    tw[k] = C2<T>{(T)cos(a), (T)sin(a)};
+    const double kk = kval(k, N, ctx->box);
+    k2[k] = (T)(kk * kk);
+  }
+  int rc;
+  if ((rc = dalloc(ctx, &g.tw, N * sizeof(C2<T>)))) return rc;
+  if ((rc = dalloc(ctx, &g.kin, N * sizeof(C2<T>)))) return rc;
+  if ((rc = dalloc(ctx, &g.k2, N * sizeof(T)))) return rc;
+  if ((rc = dalloc(ctx, &g.v_loc, ctx->ng * sizeof(T)))) return rc;
+  CK(cudaMemcpyAsync(g.tw, tw.data(), N * sizeof(C2<T>), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(g.k2, k2.data(), N * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  (void)v_host;
+  launch_convert<T>(ctx->v64, g.v_loc, ctx->ng, ctx->stream);
+  CHECK_LAUNCH("convert v_loc");
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBSE_OK;
+}
+
+// kinetic propagator per axis: exp(-i k_m^2 dt / 2); the 3D factor is the product over axes
+template <typename T> int set_kinetic(sbse_ctx *ctx, GridTables<T> &g, double dt) {
+  std::vector<C2<T>> kin(ctx->N);
+  for (int m = 0; m < ctx->N; ++m) {
+    const double kk = kval(m, ctx->N, ctx->box);
+    const double ph = -0.5 * dt * kk * kk;
+    kin[m] = C2<T>{(T)cos(ph), (T)sin(ph)};
+  }
+  CK(cudaMemcpyAsync(g.kin, kin.data(), ctx->N * sizeof(C2<T>), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBSE_OK;
+}
+
+uint64_t splitmix64_out(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int pair_index(int n_o, int i, int j) {
+  const int lo = std::min(i, j), hi = std::max(i, j);
+  return lo * n_o - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+// ---- phase timing
+void clk_begin(sbse_ctx *ctx, int phase, size_t *slot) {
+  if (!ctx->prof) return;
+  PhaseClock &c = ctx->clk;
+  if (c.used + 2 > c.ev.size()) {
+    const size_t add = std::max<size_t>(256, c.ev.size());
+    for (size_t i = 0; i < add; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c.ev.push_back(e);
+    }
+    c.phase.resize(c.ev.size() / 2 + 1);
+  }
+  *slot = c.used;
+  c.phase[c.used / 2] = phase;
+  cudaEventRecord(c.ev[c.used], ctx->stream);
+  c.used += 2;
+}
+void clk_end(sbse_ctx *ctx, size_t slot) {
+  if (!ctx->prof) return;
+  cudaEventRecord(ctx->clk.ev[slot + 1], ctx->stream);
+}
+
+// ---- templated pieces of the hot path
+
+template <typename T> GridTables<T> &tables(sbse_ctx *ctx);
+template <> GridTables<float> &tables<float>(sbse_ctx *ctx) { return ctx->g32; }
+template <> GridTables<double> &tables<double>(sbse_ctx *ctx) { return ctx->g64; }
+template <typename T> const T *phi_T(sbse_ctx *ctx);
+template <> const float *phi_T<float>(sbse_ctx *ctx) { return ctx->phi32; }
+template <> const double *phi_T<double>(sbse_ctx *ctx) { return ctx->phi64; }
+
+// u_k = v dens_k (k < n) through packed complex FFTs; acc_k += coef u_k when acc != null
+template <typename T>
+int poisson(sbse_ctx *ctx, const GridTables<T> &g, const T *dens, int n, C2<T> *pw, T *u_out,
+            double *acc, double coef) {
+  const int S = (n + 1) / 2;
+  XfwdArgs<T> xa{};
+  xa.mode = XF_PACK_DN;
+  xa.n_items = S;
+  xa.out = pw;
+  xa.dn = dens;
+  xa.n_dn = n;
+  launch_xfwd<T>(g, xa, ctx->stream);
+  launch_ypass<T>(g, pw, S, -1, ctx->stream);
+  launch_zpass<T>(g, pw, S, Z_POISSON, ctx->stream);
+  launch_ypass<T>(g, pw, S, +1, ctx->stream);
+  launch_xinv_poisson<T>(g, pw, S, n, u_out, acc, coef, 1.0, ctx->stream);
+  CHECK_LAUNCH("poisson");
+  return SBSE_OK;
+}
+
+// potentials of pair products prod[s] = (i1, j1, i2, j2) -> out (T) and/or acc (FP64, assigned)
+template <typename T>
+int poisson_products(sbse_ctx *ctx, const GridTables<T> &g, const T *orb, const int4 *prod_dev,
+                     int n_out, C2<T> *pw, T *u_out, double *acc) {
+  const int S = (n_out + 1) / 2;
+  XfwdArgs<T> xa{};
+  xa.mode = XF_PACK_PROD;
+  xa.n_items = S;
+  xa.out = pw;
+  xa.orb = orb;
+  xa.prod = prod_dev;
+  launch_xfwd<T>(g, xa, ctx->stream);
+  launch_ypass<T>(g, pw, S, -1, ctx->stream);
+  launch_zpass<T>(g, pw, S, Z_POISSON, ctx->stream);
+  launch_ypass<T>(g, pw, S, +1, ctx->stream);
+  launch_xinv_poisson<T>(g, pw, S, n_out, u_out, acc, 1.0, 0.0, ctx->stream);
+  CHECK_LAUNCH("poisson_products");
+  return SBSE_OK;
+}
+
+template <typename T>
+int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> &slots,
+                const std::vector<double> &coef_host) {
+  using C = C2<T>;
+  GridTables<T> &g = tables<T>(ctx);
+  const long long ng = ctx->ng;
+  const int P = (int)slots.size();
+  const int L = p->n_s;
+  const int S = (P + 1) / 2;
+  cudaStream_t st = ctx->stream;
+  int rc;
+  if (ctx->kin_dt != p->dt) {
+    if ((rc = set_kinetic<float>(ctx, ctx->g32, p->dt))) return rc;
+    if ((rc = set_kinetic<double>(ctx, ctx->g64, p->dt))) return rc;
+    ctx->kin_dt = p->dt;
+  }
+  void *vp;
+  C *a0, *a1, *d, *pw;
+  T *u, *dn;
+  double *wacc, *n0, *part, *cwork, *coef;
+  int4 *prod;
+  if ((rc = ensure(ctx, WS_A0, (size_t)L * ng * sizeof(C), &vp))) return rc;
+  a0 = (C *)vp;
+  if ((rc = ensure(ctx, WS_A1, (size_t)L * ng * sizeof(C), &vp))) return rc;
+  a1 = (C *)vp;
+  if ((rc = ensure(ctx, WS_D, (size_t)P * L * ng * sizeof(C), &vp))) return rc;
+  d = (C *)vp;
+  if ((rc = ensure(ctx, WS_U, (size_t)P * ng * sizeof(T), &vp))) return rc;
+  u = (T *)vp;
+  if ((rc = ensure(ctx, WS_DN, (size_t)P * ng * sizeof(T), &vp))) return rc;
+  dn = (T *)vp;
+  const size_t pw_bytes = std::max((size_t)S * ng * sizeof(C), (size_t)S * ng * sizeof(C2<double>));
+  if ((rc = ensure(ctx, WS_PW, pw_bytes, &vp))) return rc;
+  pw = (C *)vp;
+  if ((rc = ensure(ctx, WS_WACC, (size_t)P * ng * sizeof(double), &vp))) return rc;
+  wacc = (double *)vp;
+  if ((rc = ensure(ctx, WS_N0, (size_t)L * sizeof(double), &vp))) return rc;
+  n0 = (double *)vp;
+  const long long nblk = (ng + 255) / 256;
+  if ((rc = ensure(ctx, WS_PART, (size_t)nblk * L * sizeof(double), &vp))) return rc;
+  part = (double *)vp;
+  const size_t cw = clean_work_bytes<T>(ng, ctx->n_occ, P, L);
+  if ((rc = ensure(ctx, WS_CLEAN, cw, &vp))) return rc;
+  cwork = (double *)vp;
+  if ((rc = ensure(ctx, WS_COEF, coef_host.size() * sizeof(double), &vp))) return rc;
+  coef = (double *)vp;
+  if ((rc = ensure(ctx, WS_IDX, (size_t)S * sizeof(int4), &vp))) return rc;
+  prod = (int4 *)vp;
+
+  // ---- init: eta0_l (Eq. 14), N0_l, q_ij (FP64), kick
+  CK(cudaMemcpyAsync(coef, coef_host.data(), coef_host.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, st));
+  int n_part = 0;
+  launch_init_a<T>(g, ctx->phi64, ctx->n_occ, coef, L, a0, part, &n_part, st);
+  launch_reduce_cols(part, n_part, L, ctx->dV, n0, st);
+  CHECK_LAUNCH("init_a");
+  std::vector<int4> pr(S);
+  const int base = ctx->n_occ - ctx->n_o;
+  std::vector<int> pi_of(P), pj_of(P);
+  for (int k = 0; k < P; ++k) {
+    // canonical slot -> (i, j)
+    int s = slots[k], i = 0;
+    while (s >= ctx->n_o - i) { s -= ctx->n_o - i; ++i; }
+    pi_of[k] = i;
+    pj_of[k] = i + s;
+  }
+  for (int s = 0; s < S; ++s) {
+    const int k0 = 2 * s, k1 = 2 * s + 1;
+    pr[s] = make_int4(base + pi_of[k0], base + pj_of[k0], k1 < P ? base + pi_of[k1] : -1,
+                      k1 < P ? base + pj_of[k1] : -1);
+  }
+  CK(cudaMemcpyAsync(prod, pr.data(), S * sizeof(int4), cudaMemcpyHostToDevice, st));
+  if ((rc = poisson_products<double>(ctx, ctx->g64, ctx->phi64, prod, P, (C2<double> *)pw, nullptr,
+                                     wacc)))
+    return rc;
+  launch_kick<T>(g, wacc, P, a0, L, p->alpha, d, st);
+  CK(cudaMemsetAsync(u, 0, (size_t)P * ng * sizeof(T), st));
+  CHECK_LAUNCH("kick");
+
+  // ---- time loop (Eq. 10 split-operator, Eq. 15 cleaning, Eq. 13 damped trapezoid)
+  const int Nt = p->n_steps, M = p->clean_every;
+  std::vector<double> wts(Nt + 1);
+  for (int n = 0; n <= Nt; ++n) {
+    const double t = n * p->dt;
+    const double w = (n == 0 || n == Nt) ? 0.5 : 1.0;
+    wts[n] = w * exp(-0.5 * p->gamma * p->gamma * t * t) * p->dt / p->alpha;
+  }
+  C *acur = a0, *anext = a1;
+  for (int n = 0; n < Nt; ++n) {
+    bool pending = n > 0;
+    if (M > 0 && n % M == 0) {
+      size_t ck = 0;
+      clk_begin(ctx, 2, &ck);
+      if (pending) launch_half_phase<T>(g, acur, d, u, P, L, (T)(0.5 * p->dt), p->feedback, st);
+      pending = false;
+      launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw, st);
+      launch_density<T>(g, acur, d, P, L, dn, st);
+      CHECK_LAUNCH("clean");
+      if ((rc = poisson<T>(ctx, g, dn, P, pw, u, wacc, wts[n]))) return rc;
+      clk_end(ctx, ck);
+    }
+    const T tau = (T)(pending ? p->dt : 0.5 * p->dt);
+    size_t c0 = 0;
+    clk_begin(ctx, 0, &c0);
+    XfwdArgs<T> xa{};
+    xa.mode = XF_PHASE_A;
+    xa.n_items = L;
+    xa.in = acur;
+    xa.out = anext;
+    xa.tau = tau;
+    launch_xfwd<T>(g, xa, st);
+    launch_ypass<T>(g, anext, L, -1, st);
+    launch_zpass<T>(g, anext, L, Z_KINETIC, st);
+    launch_ypass<T>(g, anext, L, +1, st);
+    launch_xinv_orb<T>(g, anext, L, nullptr, L, nullptr, st);
+    XfwdArgs<T> xb{};
+    xb.mode = XF_PHASE_PAIR;
+    xb.n_items = P * L;
+    xb.in = d;
+    xb.out = d;
+    xb.a = acur;
+    xb.u = u;
+    xb.L = L;
+    xb.tau = tau;
+    xb.feedback = p->feedback;
+    launch_xfwd<T>(g, xb, st);
+    launch_ypass<T>(g, d, P * L, -1, st);
+    launch_zpass<T>(g, d, P * L, Z_KINETIC, st);
+    launch_ypass<T>(g, d, P * L, +1, st);
+    launch_xinv_orb<T>(g, d, P * L, anext, L, dn, st);
+    CHECK_LAUNCH("step");
+    clk_end(ctx, c0);
+    size_t c1 = 0;
+    clk_begin(ctx, 1, &c1);
+    const bool recomputed = (M > 0 && (n + 1) % M == 0 && n + 1 < Nt);
+    if ((rc = poisson<T>(ctx, g, dn, P, pw, u, recomputed ? nullptr : wacc,
+                         recomputed ? 0.0 : wts[n + 1])))
+      return rc;
+    clk_end(ctx, c1);
+    std::swap(acur, anext);
+  }
+  // results into the canonical slots
+  for (int k = 0; k < P; ++k)
+    CK(cudaMemcpyAsync(ctx->W + (long long)slots[k] * ng, wacc + (long long)k * ng,
+                       ng * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return SBSE_OK;
+}
+
+template <typename T> int run_build_A(sbse_ctx *ctx, unsigned terms) {
+  GridTables<T> &g = tables<T>(ctx);
+  const long long ng = ctx->ng;
+  const int n_o = ctx->n_o, n_c = ctx->n_c, n = n_o * n_c;
+  const int P = n_o * (n_o + 1) / 2;
+  const int base = ctx->n_occ - n_o;
+  cudaStream_t st = ctx->stream;
+  int rc;
+  void *vp;
+  double *K = nullptr, *Dab = nullptr;
+  size_t c3 = 0;
+  clk_begin(ctx, 3, &c3);
+  if (terms & SBSE_EXCHANGE) {
+    // potentials v(phi_j phi_b) for jb = j * n_c + b, then K = dV sum_r (phi_i phi_a)(r) U_jb(r)
+    const int S = (n + 1) / 2;
+    std::vector<int4> pr(S);
+    for (int s = 0; s < S; ++s) {
+      const int m0 = 2 * s, m1 = 2 * s + 1;
+      pr[s] = make_int4(base + m0 / n_c, ctx->n_occ + m0 % n_c, m1 < n ? base + m1 / n_c : -1,
+                        m1 < n ? ctx->n_occ + m1 % n_c : -1);
+    }
+    int4 *prod;
+    if ((rc = ensure(ctx, WS_IDX, std::max((size_t)S * sizeof(int4), (size_t)n * n_c * sizeof(int2) + 64),
+                     &vp)))
+      return rc;
+    prod = (int4 *)vp;
+    CK(cudaMemcpyAsync(prod, pr.data(), S * sizeof(int4), cudaMemcpyHostToDevice, st));
+    C2<T> *pw;
+    if ((rc = ensure(ctx, WS_PW, (size_t)S * ng * sizeof(C2<T>), &vp))) return rc;
+    pw = (C2<T> *)vp;
+    T *U;
+    if ((rc = ensure(ctx, WS_D, (size_t)n * ng * sizeof(T) + (size_t)n_c * n_c * sizeof(int2) + 256,
+                     &vp)))
+      return rc;
+    U = (T *)vp;
+    if ((rc = poisson_products<T>(ctx, g, phi_T<T>(ctx), prod, n, pw, U, nullptr))) return rc;
+    std::vector<int2> xi(n);
+    for (int m = 0; m < n; ++m) xi[m] = make_int2(base + m / n_c, ctx->n_occ + m % n_c);
+    int2 *xi_dev = (int2 *)prod;  // prod no longer needed after the Poisson passes above
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(xi_dev, xi.data(), n * sizeof(int2), cudaMemcpyHostToDevice, st));
+    if ((rc = ensure(ctx, WS_K, (size_t)n * n * sizeof(double), &vp))) return rc;
+    K = (double *)vp;
+    const size_t gw = prod_gemm_work_bytes<T>(n, n, ng);
+    if ((rc = ensure(ctx, WS_GEMM, gw, &vp))) return rc;
+    launch_prod_gemm<T>(phi_T<T>(ctx), xi_dev, n, U, n, ng, ctx->dV, K, (double *)vp, gw, st);
+    CHECK_LAUNCH("exchange");
+    CK(cudaStreamSynchronize(st));
+  }
+  if (terms & SBSE_DIRECT) {
+    for (int q = 0; q < P; ++q)
+      if (!ctx->have[q]) return fail(ctx, SBSE_ERR_NOT_READY, "W missing for some pairs: call sbse_apply_W for all n_o(n_o+1)/2 pairs first");
+    const int Mab = n_c * n_c;
+    std::vector<int2> xi(Mab);
+    for (int m = 0; m < Mab; ++m) xi[m] = make_int2(ctx->n_occ + m / n_c, ctx->n_occ + m % n_c);
+    if ((rc = ensure(ctx, WS_IDX, std::max((size_t)Mab * sizeof(int2), (size_t)16), &vp))) return rc;
+    int2 *xi_dev = (int2 *)vp;
+    CK(cudaMemcpyAsync(xi_dev, xi.data(), Mab * sizeof(int2), cudaMemcpyHostToDevice, st));
+    const T *Wt;
+    if (sizeof(T) == sizeof(double)) {
+      Wt = (const T *)ctx->W;
+    } else {
+      if ((rc = ensure(ctx, WS_U, (size_t)P * ng * sizeof(T), &vp))) return rc;
+      launch_convert<T>(ctx->W, (T *)vp, (long long)P * ng, st);
+      Wt = (const T *)vp;
+    }
+    if ((rc = ensure(ctx, WS_DAB, (size_t)Mab * P * sizeof(double), &vp))) return rc;
+    Dab = (double *)vp;
+    const size_t gw = prod_gemm_work_bytes<T>(Mab, P, ng);
+    if ((rc = ensure(ctx, WS_GEMM, gw, &vp))) return rc;
+    launch_prod_gemm<T>(phi_T<T>(ctx), xi_dev, Mab, Wt, P, ng, ctx->dV, Dab, (double *)vp, gw, st);
+    CHECK_LAUNCH("direct");
+  }
+  clk_end(ctx, c3);
+  size_t c4 = 0;
+  clk_begin(ctx, 4, &c4);
+  launch_assemble_A(ctx->eps_dev, ctx->eps_dev + n_o, n_o, n_c, ctx->scissor, K, Dab, P, ctx->A, st);
+  CHECK_LAUNCH("assemble_A");
+  clk_end(ctx, c4);
+  CK(cudaStreamSynchronize(st));
+  return SBSE_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+int sbse_create(sbse_ctx **out, int device, int precision) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return SBSE_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (precision != SBSE_FP64 && precision != SBSE_MIXED) {
+    g_create_error = "precision must be SBSE_FP64 or SBSE_MIXED";
+    return SBSE_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) {
+    g_create_error = std::string("no CUDA device ") + std::to_string(device) + ": " +
+                     (e != cudaSuccess ? cudaGetErrorString(e) : "index out of range");
+    cudaGetLastError();
+    return e != cudaSuccess ? SBSE_ERR_CUDA : SBSE_ERR_INVALID_ARG;
+  }
+  sbse_ctx *c = new (std::nothrow) sbse_ctx();
+  if (!c) {
+    g_create_error = "host allocation failed";
+    return SBSE_ERR_OOM;
+  }
+  c->device = device;
+  c->precision = precision;
+  if ((e = cudaSetDevice(device)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&c->flag, sizeof(int))) != cudaSuccess) {
+    g_create_error = std::string("CUDA setup failed: ") + cudaGetErrorString(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return SBSE_ERR_CUDA;
+  }
+  sbse::init_fft_kernels();
+  *out = c;
+  return SBSE_OK;
+}
+
+void sbse_destroy(sbse_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_grid(ctx);
+  free_scratch(ctx);
+  dfree(ctx->flag);
+  for (auto e : ctx->clk.ev) cudaEventDestroy(e);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *sbse_last_error(const sbse_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int sbse_get_stream(const sbse_ctx *ctx, void **stream) {
+  if (!ctx || !stream) return SBSE_ERR_INVALID_ARG;
+  *stream = (void *)ctx->stream;
+  return SBSE_OK;
+}
+
+int sbse_set_grid(sbse_ctx *ctx, int n, double box, const double *v_loc) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!v_loc) return fail(ctx, SBSE_ERR_INVALID_ARG, "v_loc is NULL");
+  if (!(box > 0.0) || !isfinite(box)) return fail(ctx, SBSE_ERR_INVALID_ARG, "box must be > 0");
+  FftPlan pl;
+  if (n < 4 || n > kMaxN || !make_plan(n, &pl))
+    return fail(ctx, SBSE_ERR_SHAPE, "grid edge must be 4..128 with prime factors 2, 3, 5");
+  const long long ng = (long long)n * n * n;
+  for (long long i = 0; i < ng; ++i)
+    if (!isfinite(v_loc[i])) return fail(ctx, SBSE_ERR_NUMERIC, "v_loc has NaN or Inf");
+  CK(cudaSetDevice(ctx->device));
+  free_grid(ctx);
+  ctx->N = n;
+  ctx->ng = ng;
+  ctx->box = box;
+  ctx->h = box / n;
+  ctx->dV = ctx->h * ctx->h * ctx->h;
+  int rc;
+  if ((rc = dalloc(ctx, &ctx->v64, ng * sizeof(double)))) return rc;
+  CK(cudaMemcpyAsync(ctx->v64, v_loc, ng * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if ((rc = build_tables<float>(ctx, ctx->g32, v_loc))) return rc;
+  if ((rc = build_tables<double>(ctx, ctx->g64, v_loc))) return rc;
+  return SBSE_OK;
+}
+
+int sbse_set_orbitals(sbse_ctx *ctx, int n_occ, int n_o, int n_c, const double *phi,
+                      const double *eps, double scissor) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->N == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_grid first");
+  if (!phi || !eps) return fail(ctx, SBSE_ERR_INVALID_ARG, "phi or eps is NULL");
+  if (n_occ < 1 || n_o < 1 || n_c < 1 || n_o > n_occ)
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "need 1 <= n_o <= n_occ and n_c >= 1");
+  if (!isfinite(scissor)) return fail(ctx, SBSE_ERR_NUMERIC, "scissor is not finite");
+  const int ns = n_occ + n_c;
+  const long long tot = (long long)ns * ctx->ng;
+  for (int s = 0; s < ns; ++s)
+    if (!isfinite(eps[s])) return fail(ctx, SBSE_ERR_NUMERIC, "eps has NaN or Inf");
+  for (long long i = 0; i < tot; ++i)
+    if (!isfinite(phi[i])) return fail(ctx, SBSE_ERR_NUMERIC, "phi has NaN or Inf");
+  CK(cudaSetDevice(ctx->device));
+  free_orbitals(ctx);
+  int rc;
+  if ((rc = dalloc(ctx, &ctx->phi64, tot * sizeof(double)))) return rc;
+  CK(cudaMemcpyAsync(ctx->phi64, phi, tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if ((rc = dalloc(ctx, &ctx->phi32, tot * sizeof(float)))) return rc;
+  launch_convert<float>(ctx->phi64, ctx->phi32, tot, ctx->stream);
+  CHECK_LAUNCH("convert phi");
+  std::vector<double> ew(n_o + n_c);
+  for (int i = 0; i < n_o; ++i) ew[i] = eps[n_occ - n_o + i];
+  for (int a = 0; a < n_c; ++a) ew[n_o + a] = eps[n_occ + a];
+  if ((rc = dalloc(ctx, &ctx->eps_dev, ew.size() * sizeof(double)))) return rc;
+  CK(cudaMemcpyAsync(ctx->eps_dev, ew.data(), ew.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  ctx->n_occ = n_occ;
+  ctx->n_o = n_o;
+  ctx->n_c = n_c;
+  ctx->n_states = ns;
+  ctx->scissor = scissor;
+  ctx->eps.assign(eps, eps + ns);
+  const int P = n_o * (n_o + 1) / 2;
+  if ((rc = dalloc(ctx, &ctx->W, (size_t)P * ctx->ng * sizeof(double)))) return rc;
+  ctx->have.assign(P, 0);
+  const int n = n_o * n_c;
+  if ((rc = dalloc(ctx, &ctx->A, (size_t)n * n * sizeof(double)))) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBSE_OK;
+}
+
+int sbse_coefficients(uint64_t seed, int n_s, int n_occ, int dist, double *out) {
+  if (!out || n_s < 1 || n_occ < 1 || (dist != SBSE_COEFF_GAUSSIAN && dist != SBSE_COEFF_SIGN))
+    return SBSE_ERR_INVALID_ARG;
+  const double two53 = 1.0 / 9007199254740992.0;
+  for (int l = 0; l < n_s; ++l)
+    for (int s = 0; s < n_occ; ++s) {
+      const uint64_t idx = (uint64_t)l * n_occ + s;
+      double c;
+      if (dist == SBSE_COEFF_SIGN) {
+        c = (splitmix64_out(seed, idx) >> 63) ? -1.0 : 1.0;
+      } else {
+        const double u1 = (double)(splitmix64_out(seed, 2 * idx) >> 11) * two53;
+        const double u2 = (double)(splitmix64_out(seed, 2 * idx + 1) >> 11) * two53;
+        c = sqrt(-2.0 * log(1.0 - u1)) * cos(2.0 * M_PI * u2);
+      }
+      out[(size_t)l * n_occ + s] = c;
+    }
+  return SBSE_OK;
+}
+
+int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int *pi, const int *pj,
+                 const double *coeff, double *w_out) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (!p || !pi || !pj || n_pairs < 1) return fail(ctx, SBSE_ERR_INVALID_ARG, "params/pairs missing");
+  if (p->n_s < 1 || p->n_s > 64) return fail(ctx, SBSE_ERR_INVALID_ARG, "n_s must be 1..64");
+  if (p->n_steps < 1) return fail(ctx, SBSE_ERR_INVALID_ARG, "n_steps must be >= 1");
+  if (p->clean_every < 0) return fail(ctx, SBSE_ERR_INVALID_ARG, "clean_every must be >= 0");
+  if (!(p->dt > 0.0) || !(p->alpha > 0.0) || !(p->gamma >= 0.0) || !isfinite(p->dt) ||
+      !isfinite(p->alpha) || !isfinite(p->gamma))
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "need dt > 0, alpha > 0, gamma >= 0");
+  if (p->coeff_dist != SBSE_COEFF_GAUSSIAN && p->coeff_dist != SBSE_COEFF_SIGN)
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "coeff_dist must be GAUSSIAN or SIGN");
+  const int P_all = ctx->n_o * (ctx->n_o + 1) / 2;
+  if (n_pairs > P_all) return fail(ctx, SBSE_ERR_INVALID_ARG, "more pairs than n_o(n_o+1)/2");
+  std::vector<int> slots(n_pairs);
+  std::vector<char> seen(P_all, 0);
+  for (int k = 0; k < n_pairs; ++k) {
+    if (pi[k] < 0 || pj[k] < pi[k] || pj[k] >= ctx->n_o)
+      return fail(ctx, SBSE_ERR_INVALID_ARG, "pair indices must satisfy 0 <= i <= j < n_o");
+    slots[k] = pair_index(ctx->n_o, pi[k], pj[k]);
+    if (seen[slots[k]]) return fail(ctx, SBSE_ERR_INVALID_ARG, "duplicate pair");
+    seen[slots[k]] = 1;
+  }
+  std::vector<double> c((size_t)p->n_s * ctx->n_occ);
+  if (coeff) {
+    for (size_t i = 0; i < c.size(); ++i) {
+      if (!isfinite(coeff[i])) return fail(ctx, SBSE_ERR_NUMERIC, "coeff has NaN or Inf");
+      c[i] = coeff[i];
+    }
+  } else {
+    sbse_coefficients(p->seed, p->n_s, ctx->n_occ, p->coeff_dist, c.data());
+  }
+  CK(cudaSetDevice(ctx->device));
+  ctx->have_A = false;
+  const int rc = ctx->precision == SBSE_FP64 ? run_apply_W<double>(ctx, p, slots, c)
+                                             : run_apply_W<float>(ctx, p, slots, c);
+  if (rc) return rc;
+  for (int k = 0; k < n_pairs; ++k) {
+    if (scan_nonfinite(ctx->W + (long long)slots[k] * ctx->ng, ctx->ng, ctx->flag, ctx->stream))
+      return fail(ctx, SBSE_ERR_NUMERIC, "W has NaN or Inf (unstable propagation: reduce dt)");
+    ctx->have[slots[k]] = 1;
+  }
+  if (w_out)
+    for (int k = 0; k < n_pairs; ++k)
+      CK(cudaMemcpy(w_out + (long long)k * ctx->ng, ctx->W + (long long)slots[k] * ctx->ng,
+                    ctx->ng * sizeof(double), cudaMemcpyDeviceToHost));
+  return SBSE_OK;
+}
+
+int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (terms & ~(SBSE_EXCHANGE | SBSE_DIRECT)) return fail(ctx, SBSE_ERR_INVALID_ARG, "unknown terms bits");
+  CK(cudaSetDevice(ctx->device));
+  const int rc = ctx->precision == SBSE_FP64 ? run_build_A<double>(ctx, terms)
+                                             : run_build_A<float>(ctx, terms);
+  if (rc) return rc;
+  ctx->have_A = true;
+  const int n = ctx->n_o * ctx->n_c;
+  if (a_out) CK(cudaMemcpy(a_out, ctx->A, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost));
+  return SBSE_OK;
+}
+
+int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ctx->have_A) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_build_A first");
+  const int n = ctx->n_o * ctx->n_c;
+  if (!evals || k < 1 || k > n) return fail(ctx, SBSE_ERR_INVALID_ARG, "need evals and 1 <= k <= n_o n_c");
+  if (evecs) return fail(ctx, SBSE_ERR_UNSUPPORTED, "eigenvectors are not provided by this build");
+  CK(cudaSetDevice(ctx->device));
+  void *vp;
+  int rc;
+  if ((rc = ensure(ctx, WS_EIG, eig_work_bytes(n) + (size_t)(k + 1) * sizeof(double), &vp))) return rc;
+  double *ev = (double *)vp + (long long)n * n + 2 * n;
+  size_t c4 = 0;
+  clk_begin(ctx, 4, &c4);
+  launch_eig_lowest(ctx->A, n, k, ev, (double *)vp, ctx->stream);
+  CHECK_LAUNCH("eig");
+  clk_end(ctx, c4);
+  CK(cudaMemcpyAsync(evals, ev, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < k; ++i)
+    if (!isfinite(evals[i])) return fail(ctx, SBSE_ERR_NUMERIC, "eigenvalue is not finite");
+  return SBSE_OK;
+}
+
+int sbse_profile(sbse_ctx *ctx, int enable) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->prof = enable != 0;
+  ctx->clk.used = 0;
+  return SBSE_OK;
+}
+
+int sbse_phase_time(sbse_ctx *ctx, int phase, double *ms, long long *launches) {
+  if (!ctx || !ms || !launches || phase < 0 || phase > 4) return SBSE_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  double tot = 0.0;
+  long long cnt = 0;
+  for (size_t i = 0; i + 1 < ctx->clk.used; i += 2) {
+    if (ctx->clk.phase[i / 2] != phase) continue;
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, ctx->clk.ev[i], ctx->clk.ev[i + 1]));
+    tot += f;
+    ++cnt;
+  }
+  *ms = tot;
+  *launches = cnt;
+  return SBSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,684 @@
+// Device kernels of the stochastic-TDH action of W (Sec. II.B, Eqs. 10-15).
+//
+// A 3D FFT of an item (one complex field of N^3 points, x fastest) is three batched pencil
+// passes over shared-memory tiles of 32 pencils: x (rows), y and z (columns of 32 consecutive
+// x values, coalesced). Element-wise work is fused into the passes that touch the data anyway:
+//   x forward  <- potential phase of the split-operator step (Eq. 10) or Poisson packing
+//   z          <- forward FFT, kinetic phase (or 4 pi / G^2) and 1/N^3, inverse FFT in one pass
+//   x inverse  -> induced density (Eq. 11) of all L orbitals of a pair, or the Poisson unpacking
+//                 with the damped time-integral accumulation of Eq. (13)
+#include <math.h>
+
+#include "gemm_nt.cuh"
+#include "kernels.h"
+
+namespace sbse {
+
+constexpr int kTP = 32;        // pencils per tile
+constexpr int kThreads = 256;  // threads per FFT block
+constexpr int kMaxPerThread = (kTP * kMaxN + kThreads - 1) / kThreads;
+
+template <typename T> struct GView {
+  int N;
+  long long ng;
+  FftPlan plan;
+  const C2<T> *tw;
+  const C2<T> *kin;
+  const T *k2;
+  const T *v_loc;
+};
+
+template <typename T> static GView<T> view(const GridTables<T> &g) {
+  return GView<T>{g.N, g.ng, g.plan, g.tw, g.kin, g.k2, g.v_loc};
+}
+
+template <typename T> static size_t fft_smem(int N, int tp) {
+  return (size_t)(N + 2 * N * (tp + 1)) * sizeof(C2<T>);
+}
+
+template <typename T> __device__ __forceinline__ void load_twiddles(C2<T> *tw_s, const C2<T> *tw, int N) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw_s[i] = tw[i];
+}
+
+// exp(-i x) as a complex number
+template <typename T> __device__ __forceinline__ C2<T> expmi(T x) {
+  T s, c;
+  sincos_t(x, &s, &c);
+  return C2<T>{c, -s};
+}
+
+// ------------------------------------------------------------------------------------------
+// x forward pass with fused pre-operation
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_xfwd(GView<T> g, XfwdArgs<T> a, long long rows_total) {
+  using C = C2<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const int N = g.N, ld = kTP + 1;
+  C *tw = reinterpret_cast<C *>(smem_raw);
+  C *A = tw + N;
+  C *B = A + N * ld;
+  load_twiddles<T>(tw, g.tw, N);
+  const long long N2 = (long long)N * N;
+  const long long row0 = (long long)blockIdx.x * kTP;
+  for (int l = threadIdx.x; l < kTP * N; l += blockDim.x) {
+    const int p = l / N, e = l - p * N;
+    const long long row = row0 + p;
+    C v = C{T(0), T(0)};
+    if (row < rows_total) {
+      const long long item = row / N2;
+      const long long idx = (row - item * N2) * N + e;
+      const long long gi = row * N + e;
+      if (a.mode == XF_PHASE_A) {
+        v = cmul(expmi<T>(g.v_loc[idx] * a.tau), a.in[gi]);
+      } else if (a.mode == XF_PHASE_PAIR) {
+        const int pair = (int)(item / a.L), ell = (int)(item - (long long)pair * a.L);
+        const C av = a.a[(long long)ell * g.ng + idx];
+        const C dv = a.in[gi];
+        const T uu = a.feedback ? a.u[(long long)pair * g.ng + idx] : T(0);
+        // E = exp(-i u tau), E - 1 = -2i sin(u tau/2) exp(-i u tau/2) = (-2 s^2, -2 s c)
+        T s, c;
+        sincos_t(T(0.5) * uu * a.tau, &s, &c);
+        const C em1 = C{T(-2) * s * s, T(-2) * s * c};
+        const C E = C{T(1) + em1.x, em1.y};
+        v = cmul(expmi<T>(g.v_loc[idx] * a.tau), cadd(cmul(em1, av), cmul(E, dv)));
+      } else if (a.mode == XF_PACK_DN) {
+        const long long k0 = 2 * item, k1 = 2 * item + 1;
+        v.x = a.dn[k0 * g.ng + idx];
+        v.y = (k1 < a.n_dn) ? a.dn[k1 * g.ng + idx] : T(0);
+      } else {  // XF_PACK_PROD
+        const int4 q = a.prod[item];
+        v.x = a.orb[(long long)q.x * g.ng + idx] * a.orb[(long long)q.y * g.ng + idx];
+        v.y = (q.z >= 0) ? a.orb[(long long)q.z * g.ng + idx] * a.orb[(long long)q.w * g.ng + idx]
+                         : T(0);
+      }
+    }
+    A[e * ld + p] = v;
+  }
+  __syncthreads();
+  C *R = fft_tile<T>(A, B, tw, g.plan, kTP, ld, -1);
+  for (int l = threadIdx.x; l < kTP * N; l += blockDim.x) {
+    const int p = l / N, e = l - p * N;
+    const long long row = row0 + p;
+    if (row < rows_total) a.out[row * N + e] = R[e * ld + p];
+  }
+}
+
+template <typename T> void launch_xfwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s) {
+  const long long rows = (long long)a.n_items * g.N * g.N;
+  const long long blocks = (rows + kTP - 1) / kTP;
+  k_xfwd<T><<<(unsigned)blocks, kThreads, fft_smem<T>(g.N, kTP), s>>>(view(g), a, rows);
+}
+
+// ------------------------------------------------------------------------------------------
+// y pass (forward or inverse), in place
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ypass(GView<T> g, C2<T> *data, int sign) {
+  using C = C2<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const int N = g.N, tp = N < kTP ? N : kTP, ld = tp + 1;
+  C *tw = reinterpret_cast<C *>(smem_raw);
+  C *A = tw + N;
+  C *B = A + N * ld;
+  load_twiddles<T>(tw, g.tw, N);
+  const int x0 = blockIdx.x * tp;
+  const int xt = (N - x0) < tp ? (N - x0) : tp;
+  C *base = data + (long long)blockIdx.z * g.ng + (long long)blockIdx.y * N * N + x0;
+  for (int l = threadIdx.x; l < tp * N; l += blockDim.x) {
+    const int e = l / tp, p = l - e * tp;
+    A[e * ld + p] = (p < xt) ? base[(long long)e * N + p] : C{T(0), T(0)};
+  }
+  __syncthreads();
+  C *R = fft_tile<T>(A, B, tw, g.plan, tp, ld, sign);
+  for (int l = threadIdx.x; l < tp * N; l += blockDim.x) {
+    const int e = l / tp, p = l - e * tp;
+    if (p < xt) base[(long long)e * N + p] = R[e * ld + p];
+  }
+}
+
+template <typename T>
+void launch_ypass(const GridTables<T> &g, C2<T> *data, int n_items, int sign, cudaStream_t s) {
+  const int tp = g.N < kTP ? g.N : kTP;
+  dim3 grid((g.N + tp - 1) / tp, g.N, n_items);
+  k_ypass<T><<<grid, kThreads, fft_smem<T>(g.N, tp), s>>>(view(g), data, sign);
+}
+
+// ------------------------------------------------------------------------------------------
+// z pass: forward FFT, multiply by the kinetic propagator (or the Coulomb kernel) and 1/N^3,
+// inverse FFT. The x and y passes before it have already transformed the other two axes.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_zpass(GView<T> g, C2<T> *data, int mult) {
+  using C = C2<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const int N = g.N, tp = N < kTP ? N : kTP, ld = tp + 1;
+  C *tw = reinterpret_cast<C *>(smem_raw);
+  C *A = tw + N;
+  C *B = A + N * ld;
+  load_twiddles<T>(tw, g.tw, N);
+  const int x0 = blockIdx.x * tp;
+  const int xt = (N - x0) < tp ? (N - x0) : tp;
+  const int y = blockIdx.y;
+  const long long N2 = (long long)N * N;
+  C *base = data + (long long)blockIdx.z * g.ng + (long long)y * N + x0;
+  for (int l = threadIdx.x; l < tp * N; l += blockDim.x) {
+    const int e = l / tp, p = l - e * tp;
+    A[e * ld + p] = (p < xt) ? base[(long long)e * N2 + p] : C{T(0), T(0)};
+  }
+  __syncthreads();
+  C *R = fft_tile<T>(A, B, tw, g.plan, tp, ld, -1);
+  C *S = (R == A) ? B : A;
+  const T inv_ng = T(1) / T(g.ng);
+  for (int l = threadIdx.x; l < tp * N; l += blockDim.x) {
+    const int e = l / tp, p = l - e * tp;
+    const int kx = x0 + (p < xt ? p : 0);
+    C v = R[e * ld + p];
+    if (mult == Z_KINETIC) {
+      C m = cmul(cmul(g.kin[kx], g.kin[y]), g.kin[e]);
+      v = cscale(cmul(v, m), inv_ng);
+    } else {
+      const T G2 = g.k2[kx] + g.k2[y] + g.k2[e];
+      const T f = G2 > T(0) ? T(4.0 * M_PI) / G2 * inv_ng : T(0);
+      v = cscale(v, f);
+    }
+    R[e * ld + p] = v;
+  }
+  __syncthreads();
+  C *R2 = fft_tile<T>(R, S, tw, g.plan, tp, ld, +1);
+  for (int l = threadIdx.x; l < tp * N; l += blockDim.x) {
+    const int e = l / tp, p = l - e * tp;
+    if (p < xt) base[(long long)e * N2 + p] = R2[e * ld + p];
+  }
+}
+
+template <typename T>
+void launch_zpass(const GridTables<T> &g, C2<T> *data, int n_items, int mult, cudaStream_t s) {
+  const int tp = g.N < kTP ? g.N : kTP;
+  dim3 grid((g.N + tp - 1) / tp, g.N, n_items);
+  k_zpass<T><<<grid, kThreads, fft_smem<T>(g.N, tp), s>>>(view(g), data, mult);
+}
+
+// ------------------------------------------------------------------------------------------
+// x inverse pass of orbitals, optionally with the induced density of each pair:
+// delta n = 2 sum_l (2 Re(conj(eta0_l) d_l) + |d_l|^2)  (n = 2 sum |eta|^2, Eq. 11)
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_xinv_orb(GView<T> g, C2<T> *data, long long rows_total, const C2<T> *a_next, int L, T *dens) {
+  using C = C2<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const int N = g.N, ld = kTP + 1;
+  C *tw = reinterpret_cast<C *>(smem_raw);
+  C *A = tw + N;
+  C *B = A + N * ld;
+  load_twiddles<T>(tw, g.tw, N);
+  const long long N2 = (long long)N * N;
+  if (dens == nullptr) {
+    const long long row0 = (long long)blockIdx.x * kTP;
+    for (int l = threadIdx.x; l < kTP * N; l += blockDim.x) {
+      const int p = l / N, e = l - p * N;
+      const long long row = row0 + p;
+      A[e * ld + p] = row < rows_total ? data[row * N + e] : C{T(0), T(0)};
+    }
+    __syncthreads();
+    C *R = fft_tile<T>(A, B, tw, g.plan, kTP, ld, +1);
+    for (int l = threadIdx.x; l < kTP * N; l += blockDim.x) {
+      const int p = l / N, e = l - p * N;
+      const long long row = row0 + p;
+      if (row < rows_total) data[row * N + e] = R[e * ld + p];
+    }
+    return;
+  }
+  // density mode: blockIdx.y = pair, blockIdx.x = tile of rows inside one orbital
+  const int pair = blockIdx.y;
+  const long long rr0 = (long long)blockIdx.x * kTP;
+  T acc[kMaxPerThread];
+#pragma unroll
+  for (int k = 0; k < kMaxPerThread; ++k) acc[k] = T(0);
+  for (int ell = 0; ell < L; ++ell) {
+    C *item = data + ((long long)pair * L + ell) * g.ng;
+    const C *av = a_next + (long long)ell * g.ng;
+    for (int l = threadIdx.x; l < kTP * N; l += blockDim.x) {
+      const int p = l / N, e = l - p * N;
+      const long long rr = rr0 + p;
+      A[e * ld + p] = rr < N2 ? item[rr * N + e] : C{T(0), T(0)};
+    }
+    __syncthreads();
+    C *R = fft_tile<T>(A, B, tw, g.plan, kTP, ld, +1);
+    int k = 0;
+    for (int l = threadIdx.x; l < kTP * N; l += blockDim.x, ++k) {
+      const int p = l / N, e = l - p * N;
+      const long long rr = rr0 + p;
+      if (rr < N2) {
+        const C d = R[e * ld + p];
+        item[rr * N + e] = d;
+        const C a0 = av[rr * N + e];
+        acc[k] += T(2) * (T(2) * (a0.x * d.x + a0.y * d.y) + d.x * d.x + d.y * d.y);
+      }
+    }
+    __syncthreads();
+  }
+  int k = 0;
+  for (int l = threadIdx.x; l < kTP * N; l += blockDim.x, ++k) {
+    const int p = l / N, e = l - p * N;
+    const long long rr = rr0 + p;
+    if (rr < N2) dens[(long long)pair * g.ng + rr * N + e] = acc[k];
+  }
+}
+
+template <typename T>
+void launch_xinv_orb(const GridTables<T> &g, C2<T> *data, int n_items, const C2<T> *a_next, int L,
+                     T *dens, cudaStream_t s) {
+  const size_t sm = fft_smem<T>(g.N, kTP);
+  if (dens == nullptr) {
+    const long long rows = (long long)n_items * g.N * g.N;
+    k_xinv_orb<T><<<(unsigned)((rows + kTP - 1) / kTP), kThreads, sm, s>>>(view(g), data, rows,
+                                                                            nullptr, 1, nullptr);
+  } else {
+    const long long tiles = ((long long)g.N * g.N + kTP - 1) / kTP;
+    dim3 grid((unsigned)tiles, n_items / L);
+    k_xinv_orb<T><<<grid, kThreads, sm, s>>>(view(g), data, 0, a_next, L, dens);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// x inverse pass of packed Poisson slots, unpacking two real potentials per slot and
+// accumulating the damped time integral of Eq. (13) in FP64.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_xinv_poisson(GView<T> g, const C2<T> *data, long long rows_total, int n_out, T *u_out,
+                   double *acc, double coef, double keep) {
+  using C = C2<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const int N = g.N, ld = kTP + 1;
+  C *tw = reinterpret_cast<C *>(smem_raw);
+  C *A = tw + N;
+  C *B = A + N * ld;
+  load_twiddles<T>(tw, g.tw, N);
+  const long long N2 = (long long)N * N;
+  const long long row0 = (long long)blockIdx.x * kTP;
+  for (int l = threadIdx.x; l < kTP * N; l += blockDim.x) {
+    const int p = l / N, e = l - p * N;
+    const long long row = row0 + p;
+    A[e * ld + p] = row < rows_total ? data[row * N + e] : C{T(0), T(0)};
+  }
+  __syncthreads();
+  C *R = fft_tile<T>(A, B, tw, g.plan, kTP, ld, +1);
+  for (int l = threadIdx.x; l < kTP * N; l += blockDim.x) {
+    const int p = l / N, e = l - p * N;
+    const long long row = row0 + p;
+    if (row >= rows_total) continue;
+    const long long slot = row / N2;
+    const long long idx = (row - slot * N2) * N + e;
+    const C v = R[e * ld + p];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long k = 2 * slot + h;
+      if (k >= n_out) break;
+      const T val = h ? v.y : v.x;
+      if (u_out) u_out[k * g.ng + idx] = val;
+      if (acc) {
+        double *w = acc + k * g.ng + idx;
+        *w = (keep != 0.0) ? (*w) * keep + coef * (double)val : coef * (double)val;
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_xinv_poisson(const GridTables<T> &g, C2<T> *data, int n_slots, int n_out, T *u_out,
+                         double *acc, double coef, double keep, cudaStream_t s) {
+  const long long rows = (long long)n_slots * g.N * g.N;
+  k_xinv_poisson<T><<<(unsigned)((rows + kTP - 1) / kTP), kThreads, fft_smem<T>(g.N, kTP), s>>>(
+      view(g), data, rows, n_out, u_out, acc, coef, keep);
+}
+
+// ------------------------------------------------------------------------------------------
+// initial stochastic orbitals eta_l = L^-1/2 sum_s c[l][s] phi_s (Eq. 14), FP64 sums, and the
+// per-block partial sums of |eta_l|^2 for N0_l.
+
+template <typename T>
+__global__ void k_init_a(long long ng, const double *phi, int n_occ, const double *coeff, int L,
+                         C2<T> *a, double *part) {
+  __shared__ double red[256];
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double inv = 1.0 / sqrt((double)L);
+  for (int ell = 0; ell < L; ++ell) {
+    double s = 0.0;
+    if (r < ng)
+      for (int q = 0; q < n_occ; ++q) s += coeff[(long long)ell * n_occ + q] * phi[(long long)q * ng + r];
+    s *= inv;
+    if (r < ng) a[(long long)ell * ng + r] = C2<T>{(T)s, T(0)};
+    red[threadIdx.x] = (r < ng) ? s * s : 0.0;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * L + ell] = red[0];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_init_a(const GridTables<T> &g, const double *phi, int n_occ, const double *coeff, int L,
+                   C2<T> *a, double *part, int *n_part, cudaStream_t s) {
+  const int blocks = (int)((g.ng + 255) / 256);
+  k_init_a<T><<<blocks, 256, 0, s>>>(g.ng, phi, n_occ, coeff, L, a, part);
+  *n_part = blocks;
+}
+
+// out[c] = scale * sum_{row < rows} part[row][c]  (fixed order: deterministic)
+__global__ void k_reduce_cols(const double *part, int rows, int cols, double scale, double *out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) s += part[(long long)r * cols + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = scale * red[0];
+}
+
+void launch_reduce_cols(const double *part, int rows, int cols, double scale, double *out,
+                        cudaStream_t s) {
+  if (cols > 0) k_reduce_cols<<<cols, 256, 0, s>>>(part, rows, cols, scale, out);
+}
+
+// ------------------------------------------------------------------------------------------
+// kick (Sec. II.B): d_l = (exp(-i alpha q) - 1) eta0_l = -2i sin(alpha q/2) exp(-i alpha q/2) eta0_l
+
+template <typename T>
+__global__ void k_kick(long long ng, const double *q, int P, const C2<T> *a, int L, double alpha,
+                       C2<T> *d) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int pair = blockIdx.y;
+  if (r >= ng) return;
+  double s, c;
+  sincos(0.5 * alpha * q[(long long)pair * ng + r], &s, &c);
+  const C2<T> f = C2<T>{(T)(-2.0 * s * s), (T)(-2.0 * s * c)};
+  for (int ell = 0; ell < L; ++ell)
+    d[((long long)pair * L + ell) * ng + r] = cmul(f, a[(long long)ell * ng + r]);
+}
+
+template <typename T>
+void launch_kick(const GridTables<T> &g, const double *q, int P, const C2<T> *a, int L, double alpha,
+                 C2<T> *d, cudaStream_t s) {
+  dim3 grid((unsigned)((g.ng + 255) / 256), P);
+  k_kick<T><<<grid, 256, 0, s>>>(g.ng, q, P, a, L, alpha, d);
+}
+
+// ------------------------------------------------------------------------------------------
+// pending half potential step on (eta0, d) before cleaning (same rule as the x-forward pass)
+
+template <typename T>
+__global__ void k_half_phase(GView<T> g, C2<T> *a, C2<T> *d, const T *u, int P, int L, T tau,
+                             int feedback) {
+  using C = C2<T>;
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ell = blockIdx.y;
+  if (r >= g.ng) return;
+  const C av = a[(long long)ell * g.ng + r];
+  const C pv = expmi<T>(g.v_loc[r] * tau);
+  for (int pair = 0; pair < P; ++pair) {
+    const T uu = feedback ? u[(long long)pair * g.ng + r] : T(0);
+    T s, c;
+    sincos_t(T(0.5) * uu * tau, &s, &c);
+    const C em1 = C{T(-2) * s * s, T(-2) * s * c};
+    const C E = C{T(1) + em1.x, em1.y};
+    C *dp = d + ((long long)pair * L + ell) * g.ng + r;
+    *dp = cmul(pv, cadd(cmul(em1, av), cmul(E, *dp)));
+  }
+  a[(long long)ell * g.ng + r] = cmul(pv, av);
+}
+
+template <typename T>
+void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const T *u, int P, int L, T tau,
+                       int feedback, cudaStream_t s) {
+  dim3 grid((unsigned)((g.ng + 255) / 256), L);
+  k_half_phase<T><<<grid, 256, 0, s>>>(view(g), a, d, u, P, L, tau, feedback);
+}
+
+template <typename T>
+__global__ void k_density(long long ng, const C2<T> *a, const C2<T> *d, int P, int L, T *dens) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int pair = blockIdx.y;
+  if (r >= ng) return;
+  T acc = T(0);
+  for (int ell = 0; ell < L; ++ell) {
+    const C2<T> a0 = a[(long long)ell * ng + r];
+    const C2<T> dv = d[((long long)pair * L + ell) * ng + r];
+    acc += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+  }
+  dens[(long long)pair * ng + r] = acc;
+}
+
+template <typename T>
+void launch_density(const GridTables<T> &g, const C2<T> *a, const C2<T> *d, int P, int L, T *dens,
+                    cudaStream_t s) {
+  dim3 grid((unsigned)((g.ng + 255) / 256), P);
+  k_density<T><<<grid, 256, 0, s>>>(g.ng, a, d, P, L, dens);
+}
+
+// ------------------------------------------------------------------------------------------
+// cleaning, Eq. (15): d_c <- d_c - sum_{s < N_occ} phi_s <phi_s|d_c>, then renormalisation of
+// eta^alpha = eta0 + d to its initial norm N0: d <- c d + (c - 1) eta0, c = (1 + x)^-1/2,
+// x = (2 Re<eta0|d> + |d|^2) / N0, c - 1 = -x / (sqrt(1+x) (1 + sqrt(1+x))).
+
+template <typename T> struct LoadComplexRow {  // row m = 2c + part of the complex columns d_c
+  const T *d;
+  long long ng;
+  __device__ T operator()(int m, long long k) const { return d[2 * ((long long)(m >> 1) * ng + k) + (m & 1)]; }
+};
+template <typename T> struct LoadRow {
+  const T *x;
+  long long ng;
+  __device__ T operator()(int n, long long k) const { return x[(long long)n * ng + k]; }
+};
+
+constexpr int kCleanPts = 64, kCleanCols = 16, kCleanS = 32;
+
+// d_c -= sum_s O[c][s] phi_s on a tile of 64 points x 16 columns; partial sums of
+// 2 Re(conj(eta0) d) and |d|^2 per column for the renormalisation.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_clean_update(long long ng, const T *phi, int n_occ, const double *ov /* [2c+h][s] */,
+                   C2<T> *d, const C2<T> *a, int n_cols, int L, double *npart) {
+  using C = C2<T>;
+  __shared__ T ph[kCleanS][kCleanPts];
+  __shared__ C os[kCleanCols][kCleanS + 1];
+  __shared__ double red[2][4][kCleanPts];
+  const int pt = threadIdx.x % kCleanPts;
+  const int grp = threadIdx.x / kCleanPts;  // 4 groups of 4 columns
+  const long long r0 = (long long)blockIdx.x * kCleanPts;
+  const int c0 = blockIdx.y * kCleanCols;
+  const long long r = r0 + pt;
+  C acc[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc[j] = C{T(0), T(0)};
+  for (int s0 = 0; s0 < n_occ; s0 += kCleanS) {
+    for (int l = threadIdx.x; l < kCleanS * kCleanPts; l += 256) {
+      const int ss = l / kCleanPts, pp = l % kCleanPts;
+      const int s = s0 + ss;
+      const long long rr = r0 + pp;
+      ph[ss][pp] = (s < n_occ && rr < ng) ? phi[(long long)s * ng + rr] : T(0);
+    }
+    for (int l = threadIdx.x; l < kCleanCols * kCleanS; l += 256) {
+      const int cc = l / kCleanS, ss = l % kCleanS;
+      const int c = c0 + cc, s = s0 + ss;
+      C v = C{T(0), T(0)};
+      if (c < n_cols && s < n_occ)
+        v = C{(T)ov[(long long)(2 * c) * n_occ + s], (T)ov[(long long)(2 * c + 1) * n_occ + s]};
+      os[cc][ss] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ss = 0; ss < kCleanS; ++ss) {
+      const T p = ph[ss][pt];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const C o = os[grp * 4 + j][ss];
+        acc[j].x += o.x * p;
+        acc[j].y += o.y * p;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = c0 + grp * 4 + j;
+    double v1 = 0.0, v2 = 0.0;
+    if (c < n_cols && r < ng) {
+      C *dp = d + (long long)c * ng + r;
+      C dv = *dp;
+      dv.x -= acc[j].x;
+      dv.y -= acc[j].y;
+      *dp = dv;
+      const C a0 = a[(long long)(c % L) * ng + r];
+      v1 = 2.0 * ((double)a0.x * dv.x + (double)a0.y * dv.y);
+      v2 = (double)dv.x * dv.x + (double)dv.y * dv.y;
+    }
+    red[0][grp][pt] = v1;
+    red[1][grp][pt] = v2;
+    __syncthreads();
+    for (int w = kCleanPts / 2; w > 0; w >>= 1) {
+      if (pt < w) {
+        red[0][grp][pt] += red[0][grp][pt + w];
+        red[1][grp][pt] += red[1][grp][pt + w];
+      }
+      __syncthreads();
+    }
+    if (pt == 0 && c < n_cols) {
+      npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = red[0][grp][0];
+      npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = red[1][grp][0];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_renorm(long long ng, C2<T> *d, const C2<T> *a, int n_cols, int L,
+                         const double *sums /* [c][2], times dV */, const double *n0) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (r >= ng) return;
+  const int ell = c % L;
+  const double x = (sums[2 * c] + sums[2 * c + 1]) / n0[ell];
+  const double sq = sqrt(1.0 + x);
+  const T cm1 = (T)(-x / (sq * (1.0 + sq)));
+  C2<T> *dp = d + (long long)c * ng + r;
+  const C2<T> a0 = a[(long long)ell * ng + r];
+  C2<T> dv = *dp;
+  dv.x = (T(1) + cm1) * dv.x + cm1 * a0.x;
+  dv.y = (T(1) + cm1) * dv.y + cm1 * a0.y;
+  *dp = dv;
+}
+
+template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L) {
+  const long long n_cols = (long long)P * L;
+  const long long M = 2 * n_cols;
+  const long long kc = gemm_kchunk(ng);
+  const long long chunks = (ng + kc - 1) / kc;
+  const long long ptb = (ng + kCleanPts - 1) / kCleanPts;
+  size_t b = 0;
+  b += (size_t)(chunks * M * n_occ) * sizeof(double);  // overlap partials
+  b += (size_t)(M * n_occ) * sizeof(double);           // overlaps
+  b += (size_t)(ptb * n_cols * 2) * sizeof(double);    // norm partials
+  b += (size_t)(n_cols * 2) * sizeof(double);          // norm sums
+  return b;
+}
+
+template <typename T>
+void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
+                  int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
+                  cudaStream_t s) {
+  (void)work_bytes;
+  const int n_cols = P * L;
+  const int M = 2 * n_cols;
+  const long long kc = gemm_kchunk(g.ng);
+  const long long chunks = (g.ng + kc - 1) / kc;
+  const long long ptb = (g.ng + kCleanPts - 1) / kCleanPts;
+  double *part = work;
+  double *ov = part + chunks * M * n_occ;
+  double *npart = ov + (long long)M * n_occ;
+  double *sums = npart + ptb * n_cols * 2;
+  dim3 grid((unsigned)chunks, (M + kGemmBM - 1) / kGemmBM, (n_occ + kGemmBN - 1) / kGemmBN);
+  k_gemm_nt_part<T><<<grid, kGemmThreads, 0, s>>>(
+      M, n_occ, g.ng, kc, LoadComplexRow<T>{reinterpret_cast<const T *>(d), g.ng},
+      LoadRow<T>{phi_occ, g.ng}, part);
+  launch_reduce_cols(part, (int)chunks, M * n_occ, dV, ov, s);
+  dim3 g2((unsigned)ptb, (n_cols + kCleanCols - 1) / kCleanCols);
+  k_clean_update<T><<<g2, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
+  launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
+  dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
+  k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, sums, n0);
+}
+
+// ------------------------------------------------------------------------------------------
+
+template <typename T> __global__ void k_convert(const double *src, T *dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)src[i];
+}
+template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s) {
+  if (n > 0) k_convert<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+}
+
+__global__ void k_scan_nonfinite(const double *x, long long n, int *flag) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) atomicExch(flag, 1);
+}
+int scan_nonfinite(const double *x, long long n, int *flag_dev, cudaStream_t s) {
+  int h = 0;
+  cudaMemsetAsync(flag_dev, 0, sizeof(int), s);
+  k_scan_nonfinite<<<1024, 256, 0, s>>>(x, n, flag_dev);
+  cudaMemcpyAsync(&h, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return h;
+}
+
+// one-time opt-in to large dynamic shared memory for the FFT passes
+template <typename T> static void set_smem_attrs() {
+  const int mx = (int)fft_smem<T>(kMaxN, kTP);
+  cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_ypass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv_orb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv_poisson<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+void init_fft_kernels() {
+  set_smem_attrs<float>();
+  set_smem_attrs<double>();
+}
+
+#define SBSE_INST(T)                                                                               \
+  template void launch_xfwd<T>(const GridTables<T> &, const XfwdArgs<T> &, cudaStream_t);          \
+  template void launch_ypass<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t);           \
+  template void launch_zpass<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t);           \
+  template void launch_xinv_orb<T>(const GridTables<T> &, C2<T> *, int, const C2<T> *, int, T *,   \
+                                   cudaStream_t);                                                  \
+  template void launch_xinv_poisson<T>(const GridTables<T> &, C2<T> *, int, int, T *, double *,    \
+                                       double, double, cudaStream_t);                              \
+  template void launch_init_a<T>(const GridTables<T> &, const double *, int, const double *, int,  \
+                                 C2<T> *, double *, int *, cudaStream_t);                          \
+  template void launch_kick<T>(const GridTables<T> &, const double *, int, const C2<T> *, int,     \
+                               double, C2<T> *, cudaStream_t);                                     \
+  template void launch_half_phase<T>(const GridTables<T> &, C2<T> *, C2<T> *, const T *, int, int, \
+                                     T, int, cudaStream_t);                                        \
+  template void launch_density<T>(const GridTables<T> &, const C2<T> *, const C2<T> *, int, int,   \
+                                  T *, cudaStream_t);                                              \
+  template void launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *, C2<T> *,     \
+                                int, int, const double *, double, double *, size_t, cudaStream_t); \
+  template size_t clean_work_bytes<T>(long long, int, int, int);                                   \
+  template void launch_convert<T>(const double *, T *, long long, cudaStream_t);
+
+SBSE_INST(float)
+SBSE_INST(double)
+
+}  // namespace sbse

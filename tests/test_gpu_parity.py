@@ -1,0 +1,184 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI (GPU only).
+
+Tolerances: FP64 mode, 1e-10 relative (max-norm) on W_ij, A and the excitons; mixed mode (FP32
+propagation), exciton energies within 5 meV = 1.8375e-4 Ha of the oracle and W within 2e-3
+relative (the FP32 round-off of N_t split-operator steps, each ~6e-8 relative, grows like sqrt(N_t)
+to ~1e-5 and the induced potential is a difference-form quantity, so 2e-3 leaves margin).
+"""
+import numpy as np
+import pytest
+
+import sbse_inputs as si
+from oracle import tdh
+from conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+
+MEV = 1.0 / 27211.386245988
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2205_06690_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _small_system(N, box, n_wells, seed, n_occ, n_o, n_c):
+    p = si.model_system.Preset(f"s{N}", N=N, box=box, n_wells=n_wells, seed=seed, n_occ=n_occ,
+                               n_o=n_o, n_c=n_c)
+    return si.make_system(p)
+
+
+def _gpu(B, sys_, precision, prm, n_occ, n_o, n_c, scissor, k, pairs=None, terms=3):
+    pairs = tdh.pair_list(n_o) if pairs is None else pairs
+    with B.Context(0, precision) as c:
+        c.set_grid(sys_.N, sys_.box, sys_.v_loc)
+        c.set_orbitals(n_occ, n_o, n_c, sys_.phi[:n_occ + n_c], sys_.eps[:n_occ + n_c], scissor)
+        W = c.apply_W(prm, pairs, copy_out=True)
+        A = c.build_A(terms) if len(pairs) == n_o * (n_o + 1) // 2 else None
+        ev = c.spectrum(k) if A is not None else None
+    return W, A, ev
+
+
+def _oracle(sys_, prm, n_occ, n_o, n_c, scissor, k, pairs=None):
+    g = tdh.Grid(sys_.N, sys_.box)
+    dist = "sign" if prm.coeff_dist == 1 else "gaussian"
+    coeff = tdh.stochastic_coefficients(prm.seed, prm.n_s, n_occ, dist)
+    op = tdh.TDHParams(n_steps=prm.n_steps, dt=prm.dt, gamma=prm.gamma, alpha=prm.alpha,
+                       clean_every=prm.clean_every, feedback=bool(prm.feedback))
+    return tdh.run(g, sys_.v_loc, sys_.phi, sys_.eps, n_occ, n_o, n_c, scissor, coeff, op, k,
+                   pairs=pairs)
+
+
+def test_fp64_full_path_tiny16(B, tiny16):
+    """The smallest workload, whole path: 16^3 grid, 8 electrons, 3 pairs, 200 steps."""
+    s = tiny16
+    p = s.preset
+    prm = B.TDHParams(n_s=10, n_steps=p.n_steps, clean_every=10, dt=p.dt, gamma=p.gamma,
+                      alpha=p.alpha, seed=0)
+    W, A, ev = _gpu(B, s, B.SBSE_FP64, prm, p.n_occ, p.n_o, p.n_c, p.scissor, p.n_exc)
+    ref = _oracle(s, prm, p.n_occ, p.n_o, p.n_c, p.scissor, p.n_exc)
+    for k, pr in enumerate(tdh.pair_list(p.n_o)):
+        assert rel_err(W[k].reshape(s.N, s.N, s.N), ref["W"][pr]) < 1e-10
+    assert rel_err(A, ref["A"]) < 1e-10
+    assert rel_err(ev, ref["excitons"]) < 1e-10
+
+
+@pytest.mark.parametrize("N,box,n_occ,n_o,n_c,M,dist,fb,L", [
+    (10, 6.0, 3, 3, 2, 7, 1, 1, 5),    # radix 2*5, 6 pairs, cleaning off the step grid, +-1 signs
+    (12, 7.0, 4, 2, 3, 0, 0, 1, 3),    # radix 4*3, odd pair count, no cleaning
+    (20, 8.0, 2, 1, 4, 1, 0, 0, 1),    # radix 4*5, one pair, clean every step, no feedback, L=1
+    (24, 8.0, 5, 3, 1, 4, 1, 1, 7),    # radix 4*2*3, n_c = 1
+])
+def test_fp64_ragged_grids_and_switches(B, N, box, n_occ, n_o, n_c, M, dist, fb, L):
+    s = _small_system(N, box, 3, N, n_occ, n_o, n_c)
+    prm = B.TDHParams(n_s=L, n_steps=23, clean_every=M, dt=0.05, gamma=0.2, alpha=1e-4, seed=N,
+                      coeff_dist=dist, feedback=fb)
+    k = min(3, n_o * n_c)
+    W, A, ev = _gpu(B, s, B.SBSE_FP64, prm, n_occ, n_o, n_c, 0.3, k)
+    ref = _oracle(s, prm, n_occ, n_o, n_c, 0.3, k)
+    for j, pr in enumerate(tdh.pair_list(n_o)):
+        assert rel_err(W[j].reshape(N, N, N), ref["W"][pr]) < 1e-10
+    assert rel_err(A, ref["A"]) < 1e-10
+    assert rel_err(ev, ref["excitons"]) < 1e-10
+
+
+def test_fp64_single_step_and_pair_subset(B, tiny16):
+    s = tiny16
+    prm = B.TDHParams(n_s=4, n_steps=1, clean_every=10, dt=0.05, gamma=0.1, alpha=1e-4, seed=3)
+    W, _, _ = _gpu(B, s, B.SBSE_FP64, prm, 4, 2, 4, 0.5, 2, pairs=[(1, 1)])
+    ref = _oracle(s, prm, 4, 2, 4, 0.5, 2, pairs=[(1, 1)])
+    assert rel_err(W[0].reshape(16, 16, 16), ref["W"][(1, 1)]) < 1e-10
+
+
+def test_mixed_precision_tiny16_excitons_within_5meV(B, tiny16):
+    s = tiny16
+    p = s.preset
+    prm = B.TDHParams(n_s=10, n_steps=p.n_steps, clean_every=10, dt=p.dt, gamma=p.gamma,
+                      alpha=p.alpha, seed=0)
+    W, A, ev = _gpu(B, s, B.SBSE_MIXED, prm, p.n_occ, p.n_o, p.n_c, p.scissor, p.n_exc)
+    ref = _oracle(s, prm, p.n_occ, p.n_o, p.n_c, p.scissor, p.n_exc)
+    for k, pr in enumerate(tdh.pair_list(p.n_o)):
+        assert rel_err(W[k].reshape(s.N, s.N, s.N), ref["W"][pr]) < 2e-3
+    assert np.max(np.abs(ev - ref["excitons"])) < 5 * MEV
+
+
+def test_couplings_off_gives_energy_differences(B, tiny16):
+    s = tiny16
+    with B.Context(0, B.SBSE_MIXED) as c:
+        c.set_grid(s.N, s.box, s.v_loc)
+        c.set_orbitals(4, 2, 4, s.phi, s.eps, 0.5)
+        A = c.build_A(0)
+        ev = c.spectrum(8)
+    d = np.array([s.eps[4 + a] - s.eps[2 + i] + 0.5 for i in range(2) for a in range(4)])
+    assert np.array_equal(A, np.diag(d))
+    assert np.max(np.abs(ev - np.sort(d))) < 1e-14
+
+
+def test_call_order_and_argument_errors(B, tiny16):
+    s = tiny16
+    with B.Context(0, B.SBSE_FP64) as c:
+        with pytest.raises(B.SbseError) as e:
+            c.set_orbitals(4, 2, 4, s.phi, s.eps, 0.5)
+        assert e.value.code == B.SBSE_ERR_NOT_READY
+        with pytest.raises(B.SbseError) as e:
+            c.set_grid(14, 8.0, np.zeros(14 ** 3))
+        assert e.value.code == B.SBSE_ERR_SHAPE
+        v = s.v_loc.copy()
+        v[0, 0, 0] = np.nan
+        with pytest.raises(B.SbseError) as e:
+            c.set_grid(16, 8.0, v)
+        assert e.value.code == B.SBSE_ERR_NUMERIC
+        c.set_grid(16, 8.0, s.v_loc)
+        c.set_orbitals(4, 2, 4, s.phi, s.eps, 0.5)
+        with pytest.raises(B.SbseError) as e:
+            c.spectrum(2)
+        assert e.value.code == B.SBSE_ERR_NOT_READY
+        with pytest.raises(B.SbseError) as e:
+            c.build_A(B.SBSE_DIRECT)
+        assert e.value.code == B.SBSE_ERR_NOT_READY
+        prm = B.TDHParams(n_s=2, n_steps=2)
+        for bad in ([(1, 0)], [(0, 2)], [(0, 1), (0, 1)]):
+            with pytest.raises(B.SbseError) as e:
+                c.apply_W(prm, bad)
+            assert e.value.code == B.SBSE_ERR_INVALID_ARG
+        with pytest.raises(B.SbseError) as e:
+            c.apply_W(B.TDHParams(n_s=0), [(0, 0)])
+        assert e.value.code == B.SBSE_ERR_INVALID_ARG
+        c.build_A(B.SBSE_EXCHANGE)
+        import ctypes
+        ev = np.empty(2)
+        ec = np.empty(16)
+        rc = B.load().sbse_spectrum(c.h, 2, B._dptr(ev), B._dptr(ec))
+        assert rc == B.SBSE_ERR_UNSUPPORTED
+        assert ctypes is not None
+
+
+@pytest.fixture(scope="module")
+def mid48():
+    return si.make_system(si.preset("mid48"))
+
+
+def test_mid48_full_launch_sampled_pair_fp64_and_mixed(B, mid48):
+    """The 48^3, 120-electron workload in the launch configuration of the benchmark (all 36 pairs
+    in one call, L = 10, cleaning every 10 steps), shortened to 100 steps so that the oracle can
+    recompute one sampled pair; plus the exciton energies of the two precision modes."""
+    s = mid48
+    p = s.preset
+    prm = B.TDHParams(n_s=10, n_steps=100, clean_every=10, dt=p.dt, gamma=p.gamma, alpha=p.alpha,
+                      seed=1)
+    W64, A64, ev64 = _gpu(B, s, B.SBSE_FP64, prm, p.n_occ, p.n_o, p.n_c, p.scissor, p.n_exc)
+    W32, A32, ev32 = _gpu(B, s, B.SBSE_MIXED, prm, p.n_occ, p.n_o, p.n_c, p.scissor, p.n_exc)
+    pairs = tdh.pair_list(p.n_o)
+    k = pairs.index((5, 7))
+    g = tdh.Grid(s.N, s.box)
+    coeff = tdh.stochastic_coefficients(1, 10, p.n_occ, "gaussian")
+    op = tdh.TDHParams(n_steps=100, dt=p.dt, gamma=p.gamma, alpha=p.alpha, clean_every=10)
+    phi_o = s.phi[p.n_occ - p.n_o:p.n_occ]
+    rho = phi_o[5] * phi_o[7]
+    w_ref = tdh.coulomb_periodic(rho, g) + tdh.tdh_w_pol(g, s.v_loc, s.phi[:p.n_occ], rho, coeff, op)
+    assert rel_err(W64[k].reshape(48, 48, 48), w_ref) < 1e-10
+    assert rel_err(W32[k].reshape(48, 48, 48), w_ref) < 2e-3
+    assert np.max(np.abs(A64 - A64.T)) < 1e-12
+    assert np.max(np.abs(ev32 - ev64)) < 5 * MEV
