@@ -153,6 +153,10 @@ const char *sbse_last_error(const sbse_ctx *ctx);
  * caller. Errors: INVALID_ARG. */
 int sbse_get_stream(const sbse_ctx *ctx, void **stream);
 
+/* Number of CUDA kernel launches the library has issued in this process (all contexts), for
+ * counting the kernels inside a timed region. Errors: INVALID_ARG. */
+int sbse_kernel_launches(long long *count);
+
 /* Per-phase device timing. When enabled, CUDA events bracket each phase launch group inside
  * sbse_apply_W and sbse_build_A; sbse_phase_time reports the summed device milliseconds and the
  * number of launches of one phase since the last reset (enable resets the counters).

@@ -89,6 +89,7 @@ def load() -> C.CDLL:
         "sbse_last_error": (C.c_char_p, [vp]),
         "sbse_get_stream": (i, [vp, C.POINTER(vp)]),
         "sbse_profile": (i, [vp, i]),
+        "sbse_kernel_launches": (i, [C.POINTER(C.c_longlong)]),
         "sbse_phase_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
     }
     for name, (res, args) in sig.items():
@@ -187,6 +188,12 @@ def sbse_get_stream(ctx) -> int:
     s = C.c_void_p()
     _check(ctx, load().sbse_get_stream(ctx, C.byref(s)))
     return int(s.value or 0)
+
+
+def sbse_kernel_launches() -> int:
+    n = C.c_longlong()
+    _check(None, load().sbse_kernel_launches(C.byref(n)))
+    return n.value
 
 
 def sbse_profile(ctx, enable: bool) -> None:

@@ -38,6 +38,7 @@ void launch_prod_gemm(const T *F, const int2 *xi, int M, const T *Y, int Nn, lon
   dim3 grid((unsigned)chunks, (M + kGemmBM - 1) / kGemmBM, (Nn + kGemmBN - 1) / kGemmBN);
   k_gemm_nt_part<T><<<grid, kGemmThreads, 0, s>>>(M, Nn, ng, kc, LoadProduct<T>{F, xi, ng},
                                                    LoadField<T>{Y, ng}, work);
+  count_launch(1);
   launch_reduce_cols(work, (int)chunks, M * Nn, scale, out, s);
 }
 
@@ -68,6 +69,7 @@ void launch_assemble_A(const double *eps_o, const double *eps_c, int n_o, int n_
   const long long n2 = (long long)(n_o * n_c) * (n_o * n_c);
   k_assemble_A<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(eps_o, eps_c, n_o, n_c, scissor, K, Dab,
                                                            P, A);
+  count_launch(1);
 }
 
 template size_t prod_gemm_work_bytes<float>(int, int, long long);

@@ -143,6 +143,7 @@ int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, 
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (n >= 3) {
     k_tridiag<<<1, kEigThreads, sm, s>>>(Aw, n, dg, of);
+    count_launch(1);
   } else {
     // n <= 2: the matrix is already tridiagonal
     cudaMemcpyAsync(dg, Aw, sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -152,6 +153,7 @@ int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, 
     }
   }
   k_bisect<<<(k + 127) / 128, 128, 0, s>>>(dg, of, n, k, evals_dev);
+  count_launch(1);
   return 0;
 }
 

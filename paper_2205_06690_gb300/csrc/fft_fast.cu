@@ -1,0 +1,364 @@
+// Three-pass 3D FFT round trip with compile-time N and register-resident pencils, used by the
+// split-operator step of Eq. (10), the Poisson solves of Eq. (11) / q_ij and the exchange
+// potentials of Eq. (1):
+//   plane forward  : coalesced load of PPB z-planes with the fused pre-operation into shared
+//                    memory (rows padded to N + 1), x FFT (thread per row), y FFT (thread per
+//                    column), coalesced store
+//   z column       : thread per (x, y) column, coalesced across x: forward z FFT, multiplier
+//                    (kinetic propagator exp(-i |G|^2 dt / 2) or 4 pi / |G|^2, with 1/N^3),
+//                    inverse z FFT, store
+//   plane inverse  : y and x inverse FFTs, then the fused epilogue: plain store, store plus the
+//                    induced density of all L orbitals of a pair (Eq. 11), or the Poisson
+//                    unpacking with the damped time-integral accumulation of Eq. (13)
+// Each element crosses HBM three times per round trip instead of five for the generic passes.
+#include <math.h>
+
+#include "fft_reg.cuh"
+#include "kernels.h"
+#include "passes.cuh"
+
+namespace sbse {
+
+__constant__ float2 c_twf[kRegTotal];
+__constant__ double2 c_twd[kRegTotal];
+
+template <> struct TwTab<float> {
+  __device__ __forceinline__ static float2 get(int i) { return c_twf[i]; }
+};
+template <> struct TwTab<double> {
+  __device__ __forceinline__ static double2 get(int i) { return c_twd[i]; }
+};
+
+int upload_reg_twiddles() {
+  float2 hf[kRegTotal];
+  double2 hd[kRegTotal];
+  for (int s = 0; s < kRegCount; ++s) {
+    const int N = kRegSizes[s], off = reg_offset(N);
+    for (int k = 0; k < N; ++k) {
+      const double a = -2.0 * M_PI * (double)k / (double)N;
+      hd[off + k] = make_double2(cos(a), sin(a));
+      hf[off + k] = make_float2((float)cos(a), (float)sin(a));
+    }
+  }
+  if (cudaMemcpyToSymbol(c_twf, hf, sizeof(hf)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_twd, hd, sizeof(hd)) != cudaSuccess) return -1;
+  return 0;
+}
+
+// planes per block: the largest divisor of N with <= 256 threads and <= 96 KB of shared memory
+constexpr int plane_ppb(int N, int csize) {
+  int best = 1;
+  for (int d = 1; d <= N; ++d)
+    if (N % d == 0 && d * N <= 256 && (long long)d * N * (N + 1) * csize <= 96 * 1024) best = d;
+  return best;
+}
+
+template <typename T, int N> constexpr int kPPB = plane_ppb(N, (int)sizeof(C2<T>));
+template <typename T, int N> constexpr size_t plane_smem() {
+  return (size_t)kPPB<T, N> * N * (N + 1) * sizeof(C2<T>);
+}
+
+// ------------------------------------------------------------------------------------------
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kPPB<T, N> * N)
+    k_plane_fwd(GView<T> g, XfwdArgs<T> a, long long planes_total) {
+  using C = C2<T>;
+  constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N;
+  extern __shared__ unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  const long long p0 = (long long)blockIdx.x * PPB;
+  for (int l = threadIdx.x; l < PPB * NN; l += PPB * N) {
+    const int pl = l / NN, rem = l - pl * NN, y = rem / N, x = rem - y * N;
+    const long long gp = p0 + pl;
+    C v = C{T(0), T(0)};
+    if (gp < planes_total) {
+      const long long item = gp / N;
+      const long long idx = (gp - item * N) * NN + rem;
+      v = preop_value<T>(g, a, item, idx, item * g.ng + idx);
+    }
+    S[(pl * N + y) * LD + x] = v;
+  }
+  __syncthreads();
+  const int pl = threadIdx.x / N, q = threadIdx.x - pl * N;
+  {
+    C v[N];
+    C *row = S + (pl * N + q) * LD;
+#pragma unroll
+    for (int x = 0; x < N; ++x) v[x] = row[x];
+    fft_reg<T, N, -1>(v);
+#pragma unroll
+    for (int x = 0; x < N; ++x) row[x] = v[x];
+  }
+  __syncthreads();
+  {
+    C v[N];
+    const C *col = S + pl * N * LD + q;
+#pragma unroll
+    for (int y = 0; y < N; ++y) v[y] = col[y * LD];
+    fft_reg<T, N, -1>(v);
+    const long long gp = p0 + pl;
+    if (gp < planes_total) {
+      const long long item = gp / N;
+      C *out = a.out + item * g.ng + (gp - item * N) * NN + q;
+#pragma unroll
+      for (int y = 0; y < N; ++y) out[y * N] = v[y];
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_zcol(GView<T> g, C2<T> *data, long long cols_total, int mult) {
+  using C = C2<T>;
+  constexpr int NN = N * N;
+  const long long c = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (c >= cols_total) return;
+  const long long item = c / NN;
+  const int rem = (int)(c - item * NN), y = rem / N, x = rem - y * N;
+  C *base = data + item * g.ng + rem;
+  C v[N];
+#pragma unroll
+  for (int z = 0; z < N; ++z) v[z] = base[(long long)z * NN];
+  fft_reg<T, N, -1>(v);
+  const T inv_ng = T(1) / T(N * N * N);
+  if (mult == Z_KINETIC) {
+    const C mxy = cscale(cmul(g.kin[x], g.kin[y]), inv_ng);
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = cmul(v[z], cmul(mxy, g.kin[z]));
+  } else {
+    const T gxy = g.k2[x] + g.k2[y];
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+      const T G2 = gxy + g.k2[z];
+      v[z] = cscale(v[z], G2 > T(0) ? T(4.0 * M_PI) * inv_ng / G2 : T(0));
+    }
+  }
+  fft_reg<T, N, +1>(v);
+#pragma unroll
+  for (int z = 0; z < N; ++z) base[(long long)z * NN] = v[z];
+}
+
+enum PlaneInvMode { PI_PLAIN = 0, PI_DENSITY = 1, PI_POISSON = 2 };
+
+struct PlaneInvArgs {
+  long long planes_total;  // PLAIN, POISSON: planes of all items
+  int L;                   // DENSITY: orbitals per pair
+  int n_out;               // POISSON: number of real outputs
+  double coef, keep;       // POISSON: acc = acc * keep + coef * u (assigned when keep == 0)
+};
+
+// y then x inverse transforms of PPB planes held in shared memory
+template <typename T, int N>
+__device__ __forceinline__ void plane_inverse(C2<T> *S, const C2<T> *src_item_plane0, int pl, int q) {
+  using C = C2<T>;
+  constexpr int LD = N + 1, NN = N * N;
+  {
+    C v[N];
+    const C *col = src_item_plane0 + (long long)pl * NN + q;
+#pragma unroll
+    for (int y = 0; y < N; ++y) v[y] = col[y * N];
+    fft_reg<T, N, +1>(v);
+    C *dst = S + pl * N * LD + q;
+#pragma unroll
+    for (int y = 0; y < N; ++y) dst[y * LD] = v[y];
+  }
+  __syncthreads();
+  {
+    C v[N];
+    C *row = S + (pl * N + q) * LD;
+#pragma unroll
+    for (int x = 0; x < N; ++x) v[x] = row[x];
+    fft_reg<T, N, +1>(v);
+#pragma unroll
+    for (int x = 0; x < N; ++x) row[x] = v[x];
+  }
+  __syncthreads();
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(kPPB<T, N> * N)
+    k_plane_inv(GView<T> g, C2<T> *data, const C2<T> *a_next, T *dens, T *u_out, double *acc,
+                PlaneInvArgs pa) {
+  using C = C2<T>;
+  constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N, NT = PPB * N;
+  extern __shared__ unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  const int pl = threadIdx.x / N, q = threadIdx.x - pl * N;
+  if (MODE == PI_DENSITY) {
+    // blockIdx.y = pair, blockIdx.x = group of PPB planes of each of its L orbitals
+    const int pair = blockIdx.y;
+    const int z0 = blockIdx.x * PPB;
+    T accd[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) accd[k] = T(0);
+    for (int ell = 0; ell < pa.L; ++ell) {
+      const long long item = (long long)pair * pa.L + ell;
+      C *base = data + item * g.ng + (long long)z0 * NN;
+      plane_inverse<T, N>(S, base, pl, q);
+      const C *ab = a_next + (long long)ell * g.ng + (long long)z0 * NN;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int l = threadIdx.x + k * NT;
+        const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
+        const C dv = S[(p * N + y) * LD + x];
+        base[l] = dv;
+        const C a0 = ab[l];
+        accd[k] += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+      }
+      __syncthreads();
+    }
+    T *db = dens + (long long)pair * g.ng + (long long)z0 * NN;
+#pragma unroll
+    for (int k = 0; k < N; ++k) db[threadIdx.x + k * NT] = accd[k];
+    return;
+  }
+  const long long p0 = (long long)blockIdx.x * PPB;  // PPB divides N: all planes of one item
+  const long long item = p0 / N;
+  const long long off = (p0 - item * N) * NN;
+  C *base = data + item * g.ng + off;
+  plane_inverse<T, N>(S, base, pl, q);
+#pragma unroll 4
+  for (int k = 0; k < N; ++k) {
+    const int l = threadIdx.x + k * NT;
+    const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
+    const C v = S[(p * N + y) * LD + x];
+    if (MODE == PI_PLAIN) {
+      base[l] = v;
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long kk = 2 * item + h;
+        if (kk >= pa.n_out) break;
+        const T val = h ? v.y : v.x;
+        const long long o = kk * g.ng + off + l;
+        if (u_out) u_out[o] = val;
+        if (acc) acc[o] = (pa.keep != 0.0) ? acc[o] * pa.keep + pa.coef * (double)val
+                                           : pa.coef * (double)val;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// dispatch over the compile-time sizes
+
+template <typename T, int N> static void set_attrs() {
+  const int sm = (int)plane_smem<T, N>();
+  cudaFuncSetAttribute(k_plane_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_inv<T, N, PI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_inv<T, N, PI_DENSITY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_inv<T, N, PI_POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+template <typename T> struct FastOps {
+  template <int N> static void fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s) {
+    if constexpr (!(sizeof(T) == 8 && N > 48)) {
+      const long long planes = (long long)a.n_items * N;
+      k_plane_fwd<T, N><<<(unsigned)(planes / kPPB<T, N>), kPPB<T, N> * N, plane_smem<T, N>(), s>>>(
+          view(g), a, planes);
+    }
+  }
+  template <int N> static void z(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s) {
+    if constexpr (!(sizeof(T) == 8 && N > 48)) {
+      const long long cols = (long long)n_items * N * N;
+      k_zcol<T, N><<<(unsigned)((cols + 127) / 128), 128, 0, s>>>(view(g), d, cols, mult);
+    }
+  }
+  template <int N>
+  static void inv(const GridTables<T> &g, C2<T> *d, int n_items, const C2<T> *a_next, int L, T *dens,
+                  T *u_out, double *acc, int n_out, double coef, double keep, int mode, cudaStream_t s) {
+    if constexpr (!(sizeof(T) == 8 && N > 48)) {
+      PlaneInvArgs pa{(long long)n_items * N, L, n_out, coef, keep};
+      const size_t sm = plane_smem<T, N>();
+      constexpr int NT = kPPB<T, N> * N;
+      if (mode == PI_DENSITY) {
+        dim3 grid(N / kPPB<T, N>, n_items / L);
+        k_plane_inv<T, N, PI_DENSITY><<<grid, NT, sm, s>>>(view(g), d, a_next, dens, nullptr, nullptr, pa);
+      } else if (mode == PI_PLAIN) {
+        k_plane_inv<T, N, PI_PLAIN><<<(unsigned)(pa.planes_total / kPPB<T, N>), NT, sm, s>>>(
+            view(g), d, nullptr, nullptr, nullptr, nullptr, pa);
+      } else {
+        k_plane_inv<T, N, PI_POISSON><<<(unsigned)(pa.planes_total / kPPB<T, N>), NT, sm, s>>>(
+            view(g), d, nullptr, nullptr, u_out, acc, pa);
+      }
+  }
+  }
+};
+
+#define SBSE_FAST_SWITCH(N, CALL)      \
+  switch (N) {                         \
+    case 8: CALL(8); break;            \
+    case 10: CALL(10); break;          \
+    case 12: CALL(12); break;          \
+    case 16: CALL(16); break;          \
+    case 20: CALL(20); break;          \
+    case 24: CALL(24); break;          \
+    case 32: CALL(32); break;          \
+    case 40: CALL(40); break;          \
+    case 48: CALL(48); break;          \
+    case 64: CALL(64); break;          \
+    default: break;                    \
+  }
+
+template <typename T> bool fast_supported(int N) {
+  // FP64 pencils of 64 would not fit in the register file
+  for (int i = 0; i < kRegCount; ++i)
+    if (kRegSizes[i] == N) return !(sizeof(T) == 8 && N > 48);
+  return false;
+}
+
+template <typename T> void init_fast_kernels() {
+#define SBSE_ATTR(n) set_attrs<T, n>()
+  SBSE_ATTR(8); SBSE_ATTR(10); SBSE_ATTR(12); SBSE_ATTR(16); SBSE_ATTR(20);
+  SBSE_ATTR(24); SBSE_ATTR(32); SBSE_ATTR(40); SBSE_ATTR(48);
+  if constexpr (sizeof(T) == 4) set_attrs<T, 64>();
+#undef SBSE_ATTR
+}
+
+template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s) {
+#define SBSE_CALL(n) FastOps<T>::template fwd<n>(g, a, s)
+  SBSE_FAST_SWITCH(g.N, SBSE_CALL)
+#undef SBSE_CALL
+  count_launch(1);
+}
+
+template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s) {
+#define SBSE_CALL(n) FastOps<T>::template z<n>(g, d, n_items, mult, s)
+  SBSE_FAST_SWITCH(g.N, SBSE_CALL)
+#undef SBSE_CALL
+  count_launch(1);
+}
+
+template <typename T>
+void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items, const C2<T> *a_next, int L,
+                          T *dens, cudaStream_t s) {
+  const int mode = dens ? PI_DENSITY : PI_PLAIN;
+#define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_items, a_next, L, dens, nullptr, nullptr, 0, 0.0, 0.0, mode, s)
+  SBSE_FAST_SWITCH(g.N, SBSE_CALL)
+#undef SBSE_CALL
+  count_launch(1);
+}
+
+template <typename T>
+void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, int n_out, T *u_out,
+                              double *acc, double coef, double keep, cudaStream_t s) {
+#define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, n_out, coef, keep, PI_POISSON, s)
+  SBSE_FAST_SWITCH(g.N, SBSE_CALL)
+#undef SBSE_CALL
+  count_launch(1);
+}
+
+#define SBSE_FAST_INST(T)                                                                           \
+  template bool fast_supported<T>(int);                                                            \
+  template void init_fast_kernels<T>();                                                            \
+  template void launch_plane_fwd<T>(const GridTables<T> &, const XfwdArgs<T> &, cudaStream_t);     \
+  template void launch_zcol<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t);            \
+  template void launch_plane_inv_orb<T>(const GridTables<T> &, C2<T> *, int, const C2<T> *, int,   \
+                                        T *, cudaStream_t);                                        \
+  template void launch_plane_inv_poisson<T>(const GridTables<T> &, C2<T> *, int, int, T *,         \
+                                            double *, double, double, cudaStream_t);
+
+SBSE_FAST_INST(float)
+SBSE_FAST_INST(double)
+
+}  // namespace sbse

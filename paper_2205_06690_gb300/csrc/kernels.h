@@ -19,6 +19,16 @@ template <typename T> struct GridTables {
   T *v_loc = nullptr;       // V_loc(r), ng
 };
 
+// Number of kernel launches issued by the library in this process (sbse_api.cu).
+void count_launch(int n);
+
+// ---- register-pencil three-pass round trip (fft_fast.cu), for the sizes fast_supported<T>(N)
+int upload_reg_twiddles();
+template <typename T> bool fast_supported(int N);
+template <typename T> void init_fast_kernels();
+template <typename T> struct XfwdArgs;
+template <typename T> struct GridTables;
+
 // ---- FFT passes (tdh_kernels.cu). Items are contiguous arrays of ng complex values.
 enum XfwdMode { XF_PHASE_A = 0, XF_PHASE_PAIR = 1, XF_PACK_DN = 2, XF_PACK_PROD = 3 };
 
@@ -39,6 +49,13 @@ template <typename T> struct XfwdArgs {
 };
 
 template <typename T> void launch_xfwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
+template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
+template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s);
+template <typename T> void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items,
+                                                const C2<T> *a_next, int L, T *dens, cudaStream_t s);
+template <typename T> void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots,
+                                                    int n_out, T *u_out, double *acc, double coef,
+                                                    double keep, cudaStream_t s);
 template <typename T> void launch_ypass(const GridTables<T> &g, C2<T> *data, int n_items, int sign,
                                         cudaStream_t s);
 enum ZMult { Z_KINETIC = 0, Z_POISSON = 1 };

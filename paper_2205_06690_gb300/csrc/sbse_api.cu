@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -15,6 +16,8 @@
 
 namespace sbse {
 void init_fft_kernels();
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }
 
 using namespace sbse;
@@ -273,6 +276,46 @@ template <> const float *phi_T<float>(sbse_ctx *ctx) { return ctx->phi32; }
 template <> const double *phi_T<double>(sbse_ctx *ctx) { return ctx->phi64; }
 
 // u_k = v dens_k (k < n) through packed complex FFTs; acc_k += coef u_k when acc != null
+// forward 3D FFT with the fused pre-operation, the z multiplier, and the inverse 3D FFT of the
+// orbitals of fa (n_items contiguous fields in `data`); the epilogue writes the induced density of
+// every pair (dens != null, L orbitals per pair) or just stores the propagated orbitals
+template <typename T>
+void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T> &fa, C2<T> *data,
+                         int n_items, const C2<T> *a_next, int L, T *dens) {
+  cudaStream_t st = ctx->stream;
+  if (fast_supported<T>(g.N)) {
+    launch_plane_fwd<T>(g, fa, st);
+    launch_zcol<T>(g, data, n_items, Z_KINETIC, st);
+    launch_plane_inv_orb<T>(g, data, n_items, a_next, L, dens, st);
+  } else {
+    launch_xfwd<T>(g, fa, st);
+    launch_ypass<T>(g, data, n_items, -1, st);
+    launch_zpass<T>(g, data, n_items, Z_KINETIC, st);
+    launch_ypass<T>(g, data, n_items, +1, st);
+    launch_xinv_orb<T>(g, data, n_items, a_next, L, dens, st);
+  }
+}
+
+// Poisson round trip of packed slots (fa.mode is XF_PACK_DN or XF_PACK_PROD)
+template <typename T>
+void round_trip_poisson(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T> &fa, int n_out,
+                        T *u_out, double *acc, double coef, double keep) {
+  cudaStream_t st = ctx->stream;
+  C2<T> *pw = fa.out;
+  const int S = fa.n_items;
+  if (fast_supported<T>(g.N)) {
+    launch_plane_fwd<T>(g, fa, st);
+    launch_zcol<T>(g, pw, S, Z_POISSON, st);
+    launch_plane_inv_poisson<T>(g, pw, S, n_out, u_out, acc, coef, keep, st);
+  } else {
+    launch_xfwd<T>(g, fa, st);
+    launch_ypass<T>(g, pw, S, -1, st);
+    launch_zpass<T>(g, pw, S, Z_POISSON, st);
+    launch_ypass<T>(g, pw, S, +1, st);
+    launch_xinv_poisson<T>(g, pw, S, n_out, u_out, acc, coef, keep, st);
+  }
+}
+
 template <typename T>
 int poisson(sbse_ctx *ctx, const GridTables<T> &g, const T *dens, int n, C2<T> *pw, T *u_out,
             double *acc, double coef) {
@@ -283,11 +326,7 @@ int poisson(sbse_ctx *ctx, const GridTables<T> &g, const T *dens, int n, C2<T> *
   xa.out = pw;
   xa.dn = dens;
   xa.n_dn = n;
-  launch_xfwd<T>(g, xa, ctx->stream);
-  launch_ypass<T>(g, pw, S, -1, ctx->stream);
-  launch_zpass<T>(g, pw, S, Z_POISSON, ctx->stream);
-  launch_ypass<T>(g, pw, S, +1, ctx->stream);
-  launch_xinv_poisson<T>(g, pw, S, n, u_out, acc, coef, 1.0, ctx->stream);
+  round_trip_poisson<T>(ctx, g, xa, n, u_out, acc, coef, 1.0);
   CHECK_LAUNCH("poisson");
   return SBSE_OK;
 }
@@ -303,11 +342,7 @@ int poisson_products(sbse_ctx *ctx, const GridTables<T> &g, const T *orb, const 
   xa.out = pw;
   xa.orb = orb;
   xa.prod = prod_dev;
-  launch_xfwd<T>(g, xa, ctx->stream);
-  launch_ypass<T>(g, pw, S, -1, ctx->stream);
-  launch_zpass<T>(g, pw, S, Z_POISSON, ctx->stream);
-  launch_ypass<T>(g, pw, S, +1, ctx->stream);
-  launch_xinv_poisson<T>(g, pw, S, n_out, u_out, acc, 1.0, 0.0, ctx->stream);
+  round_trip_poisson<T>(ctx, g, xa, n_out, u_out, acc, 1.0, 0.0);
   CHECK_LAUNCH("poisson_products");
   return SBSE_OK;
 }
@@ -422,11 +457,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     xa.in = acur;
     xa.out = anext;
     xa.tau = tau;
-    launch_xfwd<T>(g, xa, st);
-    launch_ypass<T>(g, anext, L, -1, st);
-    launch_zpass<T>(g, anext, L, Z_KINETIC, st);
-    launch_ypass<T>(g, anext, L, +1, st);
-    launch_xinv_orb<T>(g, anext, L, nullptr, L, nullptr, st);
+    round_trip_orbitals<T>(ctx, g, xa, anext, L, nullptr, L, nullptr);
     XfwdArgs<T> xb{};
     xb.mode = XF_PHASE_PAIR;
     xb.n_items = P * L;
@@ -437,11 +468,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     xb.L = L;
     xb.tau = tau;
     xb.feedback = p->feedback;
-    launch_xfwd<T>(g, xb, st);
-    launch_ypass<T>(g, d, P * L, -1, st);
-    launch_zpass<T>(g, d, P * L, Z_KINETIC, st);
-    launch_ypass<T>(g, d, P * L, +1, st);
-    launch_xinv_orb<T>(g, d, P * L, anext, L, dn, st);
+    round_trip_orbitals<T>(ctx, g, xb, d, P * L, anext, L, dn);
     CHECK_LAUNCH("step");
     clk_end(ctx, c0);
     size_t c1 = 0;
@@ -583,6 +610,13 @@ int sbse_create(sbse_ctx **out, int device, int precision) {
     return SBSE_ERR_CUDA;
   }
   sbse::init_fft_kernels();
+  sbse::init_fast_kernels<float>();
+  sbse::init_fast_kernels<double>();
+  if (sbse::upload_reg_twiddles() != 0) {
+    g_create_error = "upload of the FFT twiddle tables failed";
+    sbse_destroy(c);
+    return SBSE_ERR_CUDA;
+  }
   *out = c;
   return SBSE_OK;
 }
@@ -786,6 +820,12 @@ int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs) {
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < k; ++i)
     if (!isfinite(evals[i])) return fail(ctx, SBSE_ERR_NUMERIC, "eigenvalue is not finite");
+  return SBSE_OK;
+}
+
+int sbse_kernel_launches(long long *count) {
+  if (!count) return SBSE_ERR_INVALID_ARG;
+  *count = sbse::g_launches.load();
   return SBSE_OK;
 }
 

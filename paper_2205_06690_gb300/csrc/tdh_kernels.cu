@@ -11,6 +11,7 @@
 
 #include "gemm_nt.cuh"
 #include "kernels.h"
+#include "passes.cuh"
 
 namespace sbse {
 
@@ -18,33 +19,12 @@ constexpr int kTP = 32;        // pencils per tile
 constexpr int kThreads = 256;  // threads per FFT block
 constexpr int kMaxPerThread = (kTP * kMaxN + kThreads - 1) / kThreads;
 
-template <typename T> struct GView {
-  int N;
-  long long ng;
-  FftPlan plan;
-  const C2<T> *tw;
-  const C2<T> *kin;
-  const T *k2;
-  const T *v_loc;
-};
-
-template <typename T> static GView<T> view(const GridTables<T> &g) {
-  return GView<T>{g.N, g.ng, g.plan, g.tw, g.kin, g.k2, g.v_loc};
-}
-
 template <typename T> static size_t fft_smem(int N, int tp) {
   return (size_t)(N + 2 * N * (tp + 1)) * sizeof(C2<T>);
 }
 
 template <typename T> __device__ __forceinline__ void load_twiddles(C2<T> *tw_s, const C2<T> *tw, int N) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw_s[i] = tw[i];
-}
-
-// exp(-i x) as a complex number
-template <typename T> __device__ __forceinline__ C2<T> expmi(T x) {
-  T s, c;
-  sincos_t(x, &s, &c);
-  return C2<T>{c, -s};
 }
 
 // ------------------------------------------------------------------------------------------
@@ -69,29 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(GView<T> g, XfwdArgs<T> a, lo
       const long long item = row / N2;
       const long long idx = (row - item * N2) * N + e;
       const long long gi = row * N + e;
-      if (a.mode == XF_PHASE_A) {
-        v = cmul(expmi<T>(g.v_loc[idx] * a.tau), a.in[gi]);
-      } else if (a.mode == XF_PHASE_PAIR) {
-        const int pair = (int)(item / a.L), ell = (int)(item - (long long)pair * a.L);
-        const C av = a.a[(long long)ell * g.ng + idx];
-        const C dv = a.in[gi];
-        const T uu = a.feedback ? a.u[(long long)pair * g.ng + idx] : T(0);
-        // E = exp(-i u tau), E - 1 = -2i sin(u tau/2) exp(-i u tau/2) = (-2 s^2, -2 s c)
-        T s, c;
-        sincos_t(T(0.5) * uu * a.tau, &s, &c);
-        const C em1 = C{T(-2) * s * s, T(-2) * s * c};
-        const C E = C{T(1) + em1.x, em1.y};
-        v = cmul(expmi<T>(g.v_loc[idx] * a.tau), cadd(cmul(em1, av), cmul(E, dv)));
-      } else if (a.mode == XF_PACK_DN) {
-        const long long k0 = 2 * item, k1 = 2 * item + 1;
-        v.x = a.dn[k0 * g.ng + idx];
-        v.y = (k1 < a.n_dn) ? a.dn[k1 * g.ng + idx] : T(0);
-      } else {  // XF_PACK_PROD
-        const int4 q = a.prod[item];
-        v.x = a.orb[(long long)q.x * g.ng + idx] * a.orb[(long long)q.y * g.ng + idx];
-        v.y = (q.z >= 0) ? a.orb[(long long)q.z * g.ng + idx] * a.orb[(long long)q.w * g.ng + idx]
-                         : T(0);
-      }
+      v = preop_value<T>(g, a, item, idx, gi);
     }
     A[e * ld + p] = v;
   }
@@ -108,6 +66,7 @@ template <typename T> void launch_xfwd(const GridTables<T> &g, const XfwdArgs<T>
   const long long rows = (long long)a.n_items * g.N * g.N;
   const long long blocks = (rows + kTP - 1) / kTP;
   k_xfwd<T><<<(unsigned)blocks, kThreads, fft_smem<T>(g.N, kTP), s>>>(view(g), a, rows);
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -142,6 +101,7 @@ void launch_ypass(const GridTables<T> &g, C2<T> *data, int n_items, int sign, cu
   const int tp = g.N < kTP ? g.N : kTP;
   dim3 grid((g.N + tp - 1) / tp, g.N, n_items);
   k_ypass<T><<<grid, kThreads, fft_smem<T>(g.N, tp), s>>>(view(g), data, sign);
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -197,6 +157,7 @@ void launch_zpass(const GridTables<T> &g, C2<T> *data, int n_items, int mult, cu
   const int tp = g.N < kTP ? g.N : kTP;
   dim3 grid((g.N + tp - 1) / tp, g.N, n_items);
   k_zpass<T><<<grid, kThreads, fft_smem<T>(g.N, tp), s>>>(view(g), data, mult);
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -280,6 +241,7 @@ void launch_xinv_orb(const GridTables<T> &g, C2<T> *data, int n_items, const C2<
     dim3 grid((unsigned)tiles, n_items / L);
     k_xinv_orb<T><<<grid, kThreads, sm, s>>>(view(g), data, 0, a_next, L, dens);
   }
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -333,6 +295,7 @@ void launch_xinv_poisson(const GridTables<T> &g, C2<T> *data, int n_slots, int n
   const long long rows = (long long)n_slots * g.N * g.N;
   k_xinv_poisson<T><<<(unsigned)((rows + kTP - 1) / kTP), kThreads, fft_smem<T>(g.N, kTP), s>>>(
       view(g), data, rows, n_out, u_out, acc, coef, keep);
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -368,6 +331,7 @@ void launch_init_a(const GridTables<T> &g, const double *phi, int n_occ, const d
   const int blocks = (int)((g.ng + 255) / 256);
   k_init_a<T><<<blocks, 256, 0, s>>>(g.ng, phi, n_occ, coeff, L, a, part);
   *n_part = blocks;
+  count_launch(1);
 }
 
 // out[c] = scale * sum_{row < rows} part[row][c]  (fixed order: deterministic)
@@ -388,6 +352,7 @@ __global__ void k_reduce_cols(const double *part, int rows, int cols, double sca
 void launch_reduce_cols(const double *part, int rows, int cols, double scale, double *out,
                         cudaStream_t s) {
   if (cols > 0) k_reduce_cols<<<cols, 256, 0, s>>>(part, rows, cols, scale, out);
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -411,6 +376,7 @@ void launch_kick(const GridTables<T> &g, const double *q, int P, const C2<T> *a,
                  C2<T> *d, cudaStream_t s) {
   dim3 grid((unsigned)((g.ng + 255) / 256), P);
   k_kick<T><<<grid, 256, 0, s>>>(g.ng, q, P, a, L, alpha, d);
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -442,6 +408,7 @@ void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const T *u, i
                        int feedback, cudaStream_t s) {
   dim3 grid((unsigned)((g.ng + 255) / 256), L);
   k_half_phase<T><<<grid, 256, 0, s>>>(view(g), a, d, u, P, L, tau, feedback);
+  count_launch(1);
 }
 
 template <typename T>
@@ -463,6 +430,7 @@ void launch_density(const GridTables<T> &g, const C2<T> *a, const C2<T> *d, int 
                     cudaStream_t s) {
   dim3 grid((unsigned)((g.ng + 255) / 256), P);
   k_density<T><<<grid, 256, 0, s>>>(g.ng, a, d, P, L, dens);
+  count_launch(1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -617,6 +585,7 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
   launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
   dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
   k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, sums, n0);
+  count_launch(3);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -627,6 +596,7 @@ template <typename T> __global__ void k_convert(const double *src, T *dst, long 
 }
 template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s) {
   if (n > 0) k_convert<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+  count_launch(1);
 }
 
 __global__ void k_scan_nonfinite(const double *x, long long n, int *flag) {
@@ -638,6 +608,7 @@ int scan_nonfinite(const double *x, long long n, int *flag_dev, cudaStream_t s) 
   int h = 0;
   cudaMemsetAsync(flag_dev, 0, sizeof(int), s);
   k_scan_nonfinite<<<1024, 256, 0, s>>>(x, n, flag_dev);
+  count_launch(1);
   cudaMemcpyAsync(&h, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   return h;
