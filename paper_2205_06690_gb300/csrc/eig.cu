@@ -28,11 +28,20 @@ __device__ double block_sum(double v, double *red) {
 // A (n x n, row-major, overwritten) -> diagonal dg[n] and off-diagonal of[n-1].
 // H = I - beta v v^T maps A[k+1:, k] onto alpha e_1; the trailing block becomes
 // A' - v w^T - w v^T with p = beta A' v, K = beta v.p / 2, w = p - K v.
-__global__ void __launch_bounds__(kEigThreads) k_tridiag(double *A, int n, double *dg, double *of) {
+// INSMEM: the matrix is first copied to shared memory (small n), otherwise it stays in global
+// memory (L2-resident for the sizes of A).
+template <bool INSMEM>
+__global__ void __launch_bounds__(kEigThreads) k_tridiag(double *Ag, int n, double *dg, double *of) {
   extern __shared__ double sm[];
   double *v = sm;
   double *p = v + n;
   double *red = p + n;  // 33 doubles
+  double *A = Ag;
+  if (INSMEM) {
+    A = red + 34;
+    for (long long l = threadIdx.x; l < (long long)n * n; l += blockDim.x) A[l] = Ag[l];
+    __syncthreads();
+  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
@@ -106,8 +115,11 @@ __device__ int sturm_count(const double *dg, const double *of, int n, double x, 
   return c;
 }
 
+// (j+1)-th smallest eigenvalue by multisection: one warp per eigenvalue, each lane counts the
+// eigenvalues below one of 32 interior points of the bracket, which shrinks 33-fold per round.
 __global__ void k_bisect(const double *dg, const double *of, int n, int k, double *ev) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= k) return;
   double lo = dg[0], hi = dg[0], nrm = 0.0;
   for (int i = 0; i < n; ++i) {
@@ -119,16 +131,19 @@ __global__ void k_bisect(const double *dg, const double *of, int n, int k, doubl
   const double tiny = 1e-300 + 1e-30 * nrm * 2.2e-16;
   lo -= 1e-12 * (nrm + 1.0);
   hi += 1e-12 * (nrm + 1.0);
-  // find x with count(x) <= j < count(x') ... the (j+1)-th smallest eigenvalue
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(dg, of, n, mid, tiny) > j)
-      hi = mid;
-    else
-      lo = mid;
+  for (int it = 0; it < 64; ++it) {
+    const double w = (hi - lo) / 33.0;
+    const double x = lo + (lane + 1) * w;
+    const bool below = (x > lo && x < hi) ? (sturm_count(dg, of, n, x, tiny) <= j) : (x <= lo);
+    const unsigned bal = __ballot_sync(0xffffffffu, below);
+    const int m = __popc(bal);  // lanes 0..m-1 have at most j eigenvalues below their point
+    const double nlo = (m == 0) ? lo : lo + m * w;
+    const double nhi = (m == 32) ? hi : lo + (m + 1) * w;
+    if (!(nhi - nlo < hi - lo)) break;  // no further progress in floating point
+    lo = nlo;
+    hi = nhi;
   }
-  ev[j] = 0.5 * (lo + hi);
+  if (lane == 0) ev[j] = 0.5 * (lo + hi);
 }
 
 size_t eig_work_bytes(int n) { return (size_t)n * n * sizeof(double) + 2 * (size_t)n * sizeof(double); }
@@ -139,10 +154,17 @@ int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, 
   double *dg = Aw + (long long)n * n;
   double *of = dg + n;
   cudaMemcpyAsync(Aw, A, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  const size_t sm = (2 * (size_t)n + 33) * sizeof(double);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = (2 * (size_t)n + 34) * sizeof(double);
+  const size_t sm_full = sm + (size_t)n * n * sizeof(double);
   if (n >= 3) {
-    k_tridiag<<<1, kEigThreads, sm, s>>>(Aw, n, dg, of);
+    if (sm_full <= 200 * 1024) {
+      cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_full);
+      k_tridiag<true><<<1, kEigThreads, sm_full, s>>>(Aw, n, dg, of);
+    } else {
+      if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_tridiag<false><<<1, kEigThreads, sm, s>>>(Aw, n, dg, of);
+    }
     count_launch(1);
   } else {
     // n <= 2: the matrix is already tridiagonal
@@ -152,7 +174,7 @@ int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, 
       cudaMemcpyAsync(of, Aw + 2, sizeof(double), cudaMemcpyDeviceToDevice, s);
     }
   }
-  k_bisect<<<(k + 127) / 128, 128, 0, s>>>(dg, of, n, k, evals_dev);
+  k_bisect<<<(k + 7) / 8, 256, 0, s>>>(dg, of, n, k, evals_dev);
   count_launch(1);
   return 0;
 }

@@ -60,24 +60,50 @@ template <typename T, int N> constexpr size_t plane_smem() {
 
 // ------------------------------------------------------------------------------------------
 
-template <typename T, int N>
+template <typename T, int N, bool PAIR>
 __global__ void __launch_bounds__(kPPB<T, N> * N)
     k_plane_fwd(GView<T> g, XfwdArgs<T> a, long long planes_total) {
   using C = C2<T>;
-  constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N;
+  constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N, NT = PPB * N;
   extern __shared__ unsigned char smem_raw[];
   C *S = reinterpret_cast<C *>(smem_raw);
+  // PPB divides N: the block's planes z0 .. z0 + PPB - 1 are contiguous inside one item
   const long long p0 = (long long)blockIdx.x * PPB;
-  for (int l = threadIdx.x; l < PPB * NN; l += PPB * N) {
-    const int pl = l / NN, rem = l - pl * NN, y = rem / N, x = rem - y * N;
-    const long long gp = p0 + pl;
-    C v = C{T(0), T(0)};
-    if (gp < planes_total) {
-      const long long item = gp / N;
-      const long long idx = (gp - item * N) * NN + rem;
-      v = preop_value<T>(g, a, item, idx, item * g.ng + idx);
+  const long long item = p0 / N;
+  const long long off = (p0 - item * N) * NN;
+  const PreopItem<T> it = preop_item<T>(g, a, item);
+  if constexpr (PAIR) {
+    // the hot pre-operation of the pair batch: loads of 8 points are issued before any is used
+    constexpr int UB = 8;
+    const C *dp = it.in + off, *ap = it.a + off, *pp = it.pv + off;
+    const C *ep = it.em1 ? it.em1 + off : nullptr;
+#pragma unroll
+    for (int k0 = 0; k0 < N; k0 += UB) {
+      C dv[UB], av[UB], pv[UB], ev[UB];
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k0 + k < N) {
+          const int l = threadIdx.x + (k0 + k) * NT;
+          dv[k] = dp[l];
+          av[k] = ap[l];
+          pv[k] = pp[l];
+          ev[k] = ep ? ep[l] : C{T(0), T(0)};
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k0 + k < N) {
+          const int l = threadIdx.x + (k0 + k) * NT;
+          const int pl = l / NN, rem = l - pl * NN, y = rem / N, x = rem - y * N;
+          S[(pl * N + y) * LD + x] = pair_phase<T>(pv[k], ev[k], av[k], dv[k]);
+        }
+      }
     }
-    S[(pl * N + y) * LD + x] = v;
+  } else {
+    for (int l = threadIdx.x; l < PPB * NN; l += NT) {
+      const int pl = l / NN, rem = l - pl * NN, y = rem / N, x = rem - y * N;
+      S[(pl * N + y) * LD + x] = preop_at<T>(g, it, off + l);
+    }
   }
   __syncthreads();
   const int pl = threadIdx.x / N, q = threadIdx.x - pl * N;
@@ -97,13 +123,9 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
 #pragma unroll
     for (int y = 0; y < N; ++y) v[y] = col[y * LD];
     fft_reg<T, N, -1>(v);
-    const long long gp = p0 + pl;
-    if (gp < planes_total) {
-      const long long item = gp / N;
-      C *out = a.out + item * g.ng + (gp - item * N) * NN + q;
+    C *out = a.out + item * g.ng + off + pl * NN + q;
 #pragma unroll
-      for (int y = 0; y < N; ++y) out[y * N] = v[y];
-    }
+    for (int y = 0; y < N; ++y) out[y * N] = v[y];
   }
 }
 
@@ -143,8 +165,7 @@ enum PlaneInvMode { PI_PLAIN = 0, PI_DENSITY = 1, PI_POISSON = 2 };
 struct PlaneInvArgs {
   long long planes_total;  // PLAIN, POISSON: planes of all items
   int L;                   // DENSITY: orbitals per pair
-  int n_out;               // POISSON: number of real outputs
-  double coef, keep;       // POISSON: acc = acc * keep + coef * u (assigned when keep == 0)
+  PoissonOut po;           // POISSON
 };
 
 // y then x inverse transforms of PPB planes held in shared memory
@@ -177,8 +198,8 @@ __device__ __forceinline__ void plane_inverse(C2<T> *S, const C2<T> *src_item_pl
 
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(kPPB<T, N> * N)
-    k_plane_inv(GView<T> g, C2<T> *data, const C2<T> *a_next, T *dens, T *u_out, double *acc,
-                PlaneInvArgs pa) {
+    k_plane_inv(GView<T> g, C2<T> *data, const C2<T> *a_next, T *dens, T *u_out, T *acc,
+                C2<T> *em1_out, PlaneInvArgs pa) {
   using C = C2<T>;
   constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N, NT = PPB * N;
   extern __shared__ unsigned char smem_raw[];
@@ -228,12 +249,12 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const long long kk = 2 * item + h;
-        if (kk >= pa.n_out) break;
+        if (kk >= pa.po.n_out) break;
         const T val = h ? v.y : v.x;
         const long long o = kk * g.ng + off + l;
         if (u_out) u_out[o] = val;
-        if (acc) acc[o] = (pa.keep != 0.0) ? acc[o] * pa.keep + pa.coef * (double)val
-                                           : pa.coef * (double)val;
+        if (acc) acc[o] = (pa.po.keep != 0.0) ? acc[o] + (T)pa.po.coef * val : (T)pa.po.coef * val;
+        if (em1_out) em1_out[o] = phase_em1<T>(val, (T)pa.po.tau_next);
       }
     }
   }
@@ -244,7 +265,8 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
 
 template <typename T, int N> static void set_attrs() {
   const int sm = (int)plane_smem<T, N>();
-  cudaFuncSetAttribute(k_plane_fwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_fwd<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_fwd<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_DENSITY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -254,8 +276,11 @@ template <typename T> struct FastOps {
   template <int N> static void fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s) {
     if constexpr (!(sizeof(T) == 8 && N > 48)) {
       const long long planes = (long long)a.n_items * N;
-      k_plane_fwd<T, N><<<(unsigned)(planes / kPPB<T, N>), kPPB<T, N> * N, plane_smem<T, N>(), s>>>(
-          view(g), a, planes);
+      const unsigned blocks = (unsigned)(planes / kPPB<T, N>);
+      if (a.mode == XF_PHASE_PAIR)
+        k_plane_fwd<T, N, true><<<blocks, kPPB<T, N> * N, plane_smem<T, N>(), s>>>(view(g), a, planes);
+      else
+        k_plane_fwd<T, N, false><<<blocks, kPPB<T, N> * N, plane_smem<T, N>(), s>>>(view(g), a, planes);
     }
   }
   template <int N> static void z(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s) {
@@ -266,20 +291,21 @@ template <typename T> struct FastOps {
   }
   template <int N>
   static void inv(const GridTables<T> &g, C2<T> *d, int n_items, const C2<T> *a_next, int L, T *dens,
-                  T *u_out, double *acc, int n_out, double coef, double keep, int mode, cudaStream_t s) {
+                  T *u_out, T *acc, C2<T> *em1_out, const PoissonOut &po, int mode, cudaStream_t s) {
     if constexpr (!(sizeof(T) == 8 && N > 48)) {
-      PlaneInvArgs pa{(long long)n_items * N, L, n_out, coef, keep};
+      PlaneInvArgs pa{(long long)n_items * N, L, po};
       const size_t sm = plane_smem<T, N>();
       constexpr int NT = kPPB<T, N> * N;
       if (mode == PI_DENSITY) {
         dim3 grid(N / kPPB<T, N>, n_items / L);
-        k_plane_inv<T, N, PI_DENSITY><<<grid, NT, sm, s>>>(view(g), d, a_next, dens, nullptr, nullptr, pa);
+        k_plane_inv<T, N, PI_DENSITY><<<grid, NT, sm, s>>>(view(g), d, a_next, dens, nullptr, nullptr,
+                                                            nullptr, pa);
       } else if (mode == PI_PLAIN) {
         k_plane_inv<T, N, PI_PLAIN><<<(unsigned)(pa.planes_total / kPPB<T, N>), NT, sm, s>>>(
-            view(g), d, nullptr, nullptr, nullptr, nullptr, pa);
+            view(g), d, nullptr, nullptr, nullptr, nullptr, nullptr, pa);
       } else {
         k_plane_inv<T, N, PI_POISSON><<<(unsigned)(pa.planes_total / kPPB<T, N>), NT, sm, s>>>(
-            view(g), d, nullptr, nullptr, u_out, acc, pa);
+            view(g), d, nullptr, nullptr, u_out, acc, em1_out, pa);
       }
   }
   }
@@ -333,16 +359,17 @@ template <typename T>
 void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items, const C2<T> *a_next, int L,
                           T *dens, cudaStream_t s) {
   const int mode = dens ? PI_DENSITY : PI_PLAIN;
-#define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_items, a_next, L, dens, nullptr, nullptr, 0, 0.0, 0.0, mode, s)
+  const PoissonOut po{0, 0.0, 0.0, 0.0};
+#define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_items, a_next, L, dens, nullptr, nullptr, nullptr, po, mode, s)
   SBSE_FAST_SWITCH(g.N, SBSE_CALL)
 #undef SBSE_CALL
   count_launch(1);
 }
 
 template <typename T>
-void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, int n_out, T *u_out,
-                              double *acc, double coef, double keep, cudaStream_t s) {
-#define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, n_out, coef, keep, PI_POISSON, s)
+void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, const PoissonOut &po,
+                              T *u_out, T *acc, C2<T> *em1_out, cudaStream_t s) {
+#define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, em1_out, po, PI_POISSON, s)
   SBSE_FAST_SWITCH(g.N, SBSE_CALL)
 #undef SBSE_CALL
   count_launch(1);
@@ -355,8 +382,8 @@ void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, int
   template void launch_zcol<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t);            \
   template void launch_plane_inv_orb<T>(const GridTables<T> &, C2<T> *, int, const C2<T> *, int,   \
                                         T *, cudaStream_t);                                        \
-  template void launch_plane_inv_poisson<T>(const GridTables<T> &, C2<T> *, int, int, T *,         \
-                                            double *, double, double, cudaStream_t);
+  template void launch_plane_inv_poisson<T>(const GridTables<T> &, C2<T> *, int, const PoissonOut &, \
+                                            T *, T *, C2<T> *, cudaStream_t);
 
 SBSE_FAST_INST(float)
 SBSE_FAST_INST(double)

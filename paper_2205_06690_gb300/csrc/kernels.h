@@ -17,6 +17,8 @@ template <typename T> struct GridTables {
   C2<T> *kin = nullptr;     // exp(-i k_m^2 dt / 2) per axis index m (rebuilt per dt)
   T *k2 = nullptr;          // k_m^2 per axis index m
   T *v_loc = nullptr;       // V_loc(r), ng
+  C2<T> *pv_dt = nullptr;   // exp(-i V_loc dt), ng (rebuilt per dt)
+  C2<T> *pv_half = nullptr; // exp(-i V_loc dt / 2), ng
 };
 
 // Number of kernel launches issued by the library in this process (sbse_api.cu).
@@ -38,10 +40,9 @@ template <typename T> struct XfwdArgs {
   const C2<T> *in;       // A: a_cur; PAIR: d (in place)
   C2<T> *out;            // A: a_next; PAIR: d; PACK: packed work buffer
   const C2<T> *a;        // PAIR: a_cur
-  const T *u;            // PAIR: u per pair (ng each)
+  const C2<T> *pv;       // A, PAIR: exp(-i V_loc tau) per grid point (tau = dt or dt/2)
+  const C2<T> *em1;      // PAIR: exp(-i u tau) - 1 per pair (ng each); null -> u ignored
   int L;                 // PAIR: orbitals per pair
-  T tau;                 // phase time: V, u multiplied by tau (dt or dt/2)
-  int feedback;          // PAIR: 0 -> u ignored
   const T *dn;           // PACK_DN: density per pair; slot s packs 2s (re) and 2s+1 (im)
   int n_dn;              // PACK_DN: number of densities
   const T *orb;          // PACK_PROD: orbital rows (ng each)
@@ -53,9 +54,20 @@ template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdAr
 template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s);
 template <typename T> void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items,
                                                 const C2<T> *a_next, int L, T *dens, cudaStream_t s);
+// Poisson epilogue outputs of slot pair k: u_out[k] = u, acc[k] (+)= coef u, and, when em1_out is
+// not null, em1_out[k] = exp(-i u tau_next) - 1 = -2i sin(u tau_next/2) exp(-i u tau_next/2), the
+// potential factor of the next split-operator step.
+struct PoissonOut {
+  int n_out;
+  double coef, keep;
+  double tau_next;
+};
 template <typename T> void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots,
-                                                    int n_out, T *u_out, double *acc, double coef,
-                                                    double keep, cudaStream_t s);
+                                                    const PoissonOut &po, T *u_out, T *acc,
+                                                    C2<T> *em1_out, cudaStream_t s);
+// out = exp(-i V_loc tau), computed in FP64 from the FP64 potential v64
+template <typename T> void launch_phase_table(const double *v64, long long ng, double tau, C2<T> *out,
+                                              cudaStream_t s);
 template <typename T> void launch_ypass(const GridTables<T> &g, C2<T> *data, int n_items, int sign,
                                         cudaStream_t s);
 enum ZMult { Z_KINETIC = 0, Z_POISSON = 1 };
@@ -66,10 +78,13 @@ template <typename T> void launch_zpass(const GridTables<T> &g, C2<T> *data, int
 template <typename T> void launch_xinv_orb(const GridTables<T> &g, C2<T> *data, int n_items,
                                            const C2<T> *a_next, int L, T *dens, cudaStream_t s);
 // inverse x pass of packed Poisson slots: potential of density 2s (re) / 2s+1 (im) ->
-// u_out[k] (if non-null) and acc[k] = acc[k] * keep + coef * value (if acc non-null), k < n_out.
+// u_out[k] (if non-null) and acc[k] = acc[k] + coef * value, or coef * value when keep == 0
+// (if acc non-null), k < n_out.
 template <typename T> void launch_xinv_poisson(const GridTables<T> &g, C2<T> *data, int n_slots,
-                                               int n_out, T *u_out, double *acc, double coef,
-                                               double keep, cudaStream_t s);
+                                               const PoissonOut &po, T *u_out, T *acc,
+                                               C2<T> *em1_out, cudaStream_t s);
+// acc64 += acc, acc = 0
+template <typename T> void launch_flush_acc(double *acc64, T *acc, long long n, cudaStream_t s);
 
 // ---- elementwise and reduction kernels (tdh_kernels.cu)
 template <typename T> void launch_init_a(const GridTables<T> &g, const double *phi, int n_occ,

@@ -21,6 +21,14 @@ template <typename T> static GView<T> view(const GridTables<T> &g) {
   return GView<T>{g.N, g.ng, g.plan, g.tw, g.kin, g.k2, g.v_loc};
 }
 
+// E - 1 = exp(-i u tau) - 1 = -2i sin(u tau/2) exp(-i u tau/2) = (-2 s^2, -2 s c), without the
+// cancellation of 1 - cos(u tau) (u tau is O(alpha))
+template <typename T> __device__ __forceinline__ C2<T> phase_em1(T u, T tau) {
+  T s, c;
+  sincos_t(T(0.5) * u * tau, &s, &c);
+  return C2<T>{T(-2) * s * s, T(-2) * s * c};
+}
+
 // exp(-i x) as a complex number
 template <typename T> __device__ __forceinline__ C2<T> expmi(T x) {
   T s, c;
@@ -28,36 +36,70 @@ template <typename T> __device__ __forceinline__ C2<T> expmi(T x) {
   return C2<T>{c, -s};
 }
 
-// Value entering the forward transform at grid point idx of item `item` (gi = item * ng + idx):
-//  XF_PHASE_A    P a                                  with P = exp(-i V tau)
-//  XF_PHASE_PAIR P [(E - 1) a + E d]                  with E = exp(-i u tau) (u = 0 without feedback),
-//                E - 1 = -2i sin(u tau/2) exp(-i u tau/2): the potential part of the split-operator
-//                step of Eq. (10) on the difference d = eta^alpha - eta0 of one stochastic orbital
+// Value entering the forward transform at grid point idx of one item:
+//  XF_PHASE_A    P a                                  with P = exp(-i V tau) (precomputed table)
+//  XF_PHASE_PAIR P [(E - 1) a + E d]                  with E - 1 = exp(-i u tau) - 1 precomputed per
+//                pair by the Poisson epilogue (E = 1 without feedback): the potential part of the
+//                split-operator step of Eq. (10) on the difference d = eta^alpha - eta0
 //  XF_PACK_DN    dn[2 item] + i dn[2 item + 1]        (two real densities per complex transform)
 //  XF_PACK_PROD  phi_i1 phi_j1 + i phi_i2 phi_j2      (pair products, for q_ij and (ia|jb))
+// The per-item pointers are resolved once (preop_item) and then indexed per point (preop_at).
+template <typename T> struct PreopItem {
+  int mode;
+  const C2<T> *in;   // PHASE_A, PHASE_PAIR
+  const C2<T> *a;    // PHASE_PAIR: eta0 of the same stochastic orbital
+  const C2<T> *em1;  // PHASE_PAIR: E - 1 of the pair (null: no feedback)
+  const C2<T> *pv;   // PHASE_A, PHASE_PAIR
+  const T *r0, *r1, *r2, *r3;  // PACK_DN: r0 (re), r1 (im or null); PACK_PROD: r0 r1 (re), r2 r3 (im)
+};
+
+template <typename T>
+__device__ __forceinline__ PreopItem<T> preop_item(const GView<T> &g, const XfwdArgs<T> &a, long long item) {
+  PreopItem<T> it{};
+  it.mode = a.mode;
+  it.pv = a.pv;
+  if (a.mode == XF_PHASE_A) {
+    it.in = a.in + item * g.ng;
+  } else if (a.mode == XF_PHASE_PAIR) {
+    const int itm = (int)item;
+    const int pair = itm / a.L, ell = itm - pair * a.L;
+    it.in = a.in + item * g.ng;
+    it.a = a.a + (long long)ell * g.ng;
+    it.em1 = a.em1 ? a.em1 + (long long)pair * g.ng : nullptr;
+  } else if (a.mode == XF_PACK_DN) {
+    it.r0 = a.dn + 2 * item * g.ng;
+    it.r1 = (2 * item + 1 < a.n_dn) ? a.dn + (2 * item + 1) * g.ng : nullptr;
+  } else {
+    const int4 q = a.prod[item];
+    it.r0 = a.orb + (long long)q.x * g.ng;
+    it.r1 = a.orb + (long long)q.y * g.ng;
+    it.r2 = q.z >= 0 ? a.orb + (long long)q.z * g.ng : nullptr;
+    it.r3 = q.z >= 0 ? a.orb + (long long)q.w * g.ng : nullptr;
+  }
+  return it;
+}
+
+template <typename T>
+__device__ __forceinline__ C2<T> pair_phase(C2<T> pv, C2<T> em1, C2<T> av, C2<T> dv) {
+  const C2<T> E = C2<T>{T(1) + em1.x, em1.y};
+  return cmul(pv, cadd(cmul(em1, av), cmul(E, dv)));
+}
+
+template <typename T>
+__device__ __forceinline__ C2<T> preop_at(const GView<T> &g, const PreopItem<T> &it, long long idx) {
+  using C = C2<T>;
+  if (it.mode == XF_PHASE_A) return cmul(it.pv[idx], it.in[idx]);
+  if (it.mode == XF_PHASE_PAIR)
+    return pair_phase<T>(it.pv[idx], it.em1 ? it.em1[idx] : C{T(0), T(0)}, it.a[idx], it.in[idx]);
+  if (it.mode == XF_PACK_DN) return C{it.r0[idx], it.r1 ? it.r1[idx] : T(0)};
+  return C{it.r0[idx] * it.r1[idx], it.r2 ? it.r2[idx] * it.r3[idx] : T(0)};
+}
+
 template <typename T>
 __device__ __forceinline__ C2<T> preop_value(const GView<T> &g, const XfwdArgs<T> &a, long long item,
                                              long long idx, long long gi) {
-  using C = C2<T>;
-  if (a.mode == XF_PHASE_A) return cmul(expmi<T>(g.v_loc[idx] * a.tau), a.in[gi]);
-  if (a.mode == XF_PHASE_PAIR) {
-    const int pair = (int)(item / a.L), ell = (int)(item - (long long)pair * a.L);
-    const C av = a.a[(long long)ell * g.ng + idx];
-    const C dv = a.in[gi];
-    const T uu = a.feedback ? a.u[(long long)pair * g.ng + idx] : T(0);
-    T s, c;
-    sincos_t(T(0.5) * uu * a.tau, &s, &c);
-    const C em1 = C{T(-2) * s * s, T(-2) * s * c};
-    const C E = C{T(1) + em1.x, em1.y};
-    return cmul(expmi<T>(g.v_loc[idx] * a.tau), cadd(cmul(em1, av), cmul(E, dv)));
-  }
-  if (a.mode == XF_PACK_DN) {
-    const long long k0 = 2 * item, k1 = 2 * item + 1;
-    return C{a.dn[k0 * g.ng + idx], (k1 < a.n_dn) ? a.dn[k1 * g.ng + idx] : T(0)};
-  }
-  const int4 q = a.prod[item];
-  return C{a.orb[(long long)q.x * g.ng + idx] * a.orb[(long long)q.y * g.ng + idx],
-           (q.z >= 0) ? a.orb[(long long)q.z * g.ng + idx] * a.orb[(long long)q.w * g.ng + idx] : T(0)};
+  (void)gi;
+  return preop_at<T>(g, preop_item<T>(g, a, item), idx);
 }
 
 }  // namespace sbse

@@ -65,7 +65,7 @@ struct sbse_ctx {
   double *A = nullptr;
   bool have_A = false;
   // scratch
-  DevBuf ws[16];
+  DevBuf ws[24];
   int *flag = nullptr;
   // profiling
   bool prof = false;
@@ -76,7 +76,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -157,6 +157,8 @@ void free_orbitals(sbse_ctx *ctx) {
 }
 
 template <typename T> void free_tables(GridTables<T> &g) {
+  dfree(g.pv_dt);
+  dfree(g.pv_half);
   dfree(g.tw);
   dfree(g.kin);
   dfree(g.k2);
@@ -209,6 +211,8 @@ template <typename T> int build_tables(sbse_ctx *ctx, GridTables<T> &g, const do
   if ((rc = dalloc(ctx, &g.kin, N * sizeof(C2<T>)))) return rc;
   if ((rc = dalloc(ctx, &g.k2, N * sizeof(T)))) return rc;
   if ((rc = dalloc(ctx, &g.v_loc, ctx->ng * sizeof(T)))) return rc;
+  if ((rc = dalloc(ctx, &g.pv_dt, ctx->ng * sizeof(C2<T>)))) return rc;
+  if ((rc = dalloc(ctx, &g.pv_half, ctx->ng * sizeof(C2<T>)))) return rc;
   CK(cudaMemcpyAsync(g.tw, tw.data(), N * sizeof(C2<T>), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(g.k2, k2.data(), N * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
   (void)v_host;
@@ -227,6 +231,10 @@ template <typename T> int set_kinetic(sbse_ctx *ctx, GridTables<T> &g, double dt
     kin[m] = C2<T>{(T)cos(ph), (T)sin(ph)};
   }
   CK(cudaMemcpyAsync(g.kin, kin.data(), ctx->N * sizeof(C2<T>), cudaMemcpyHostToDevice, ctx->stream));
+  // potential factors exp(-i V dt) (two merged half steps) and exp(-i V dt / 2)
+  launch_phase_table<T>(ctx->v64, ctx->ng, dt, g.pv_dt, ctx->stream);
+  launch_phase_table<T>(ctx->v64, ctx->ng, 0.5 * dt, g.pv_half, ctx->stream);
+  CHECK_LAUNCH("phase tables");
   CK(cudaStreamSynchronize(ctx->stream));
   return SBSE_OK;
 }
@@ -298,27 +306,28 @@ void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T
 
 // Poisson round trip of packed slots (fa.mode is XF_PACK_DN or XF_PACK_PROD)
 template <typename T>
-void round_trip_poisson(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T> &fa, int n_out,
-                        T *u_out, double *acc, double coef, double keep) {
+void round_trip_poisson(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T> &fa,
+                        const PoissonOut &po, T *u_out, T *acc, C2<T> *em1_out) {
   cudaStream_t st = ctx->stream;
   C2<T> *pw = fa.out;
   const int S = fa.n_items;
   if (fast_supported<T>(g.N)) {
     launch_plane_fwd<T>(g, fa, st);
     launch_zcol<T>(g, pw, S, Z_POISSON, st);
-    launch_plane_inv_poisson<T>(g, pw, S, n_out, u_out, acc, coef, keep, st);
+    launch_plane_inv_poisson<T>(g, pw, S, po, u_out, acc, em1_out, st);
   } else {
     launch_xfwd<T>(g, fa, st);
     launch_ypass<T>(g, pw, S, -1, st);
     launch_zpass<T>(g, pw, S, Z_POISSON, st);
     launch_ypass<T>(g, pw, S, +1, st);
-    launch_xinv_poisson<T>(g, pw, S, n_out, u_out, acc, coef, keep, st);
+    launch_xinv_poisson<T>(g, pw, S, po, u_out, acc, em1_out, st);
   }
 }
 
+// u_k = v dens_k; acc_k += coef u_k (acc != null); em1_k = exp(-i u_k tau_next) - 1 (em1 != null)
 template <typename T>
 int poisson(sbse_ctx *ctx, const GridTables<T> &g, const T *dens, int n, C2<T> *pw, T *u_out,
-            double *acc, double coef) {
+            T *acc, double coef, C2<T> *em1, double tau_next) {
   const int S = (n + 1) / 2;
   XfwdArgs<T> xa{};
   xa.mode = XF_PACK_DN;
@@ -326,7 +335,7 @@ int poisson(sbse_ctx *ctx, const GridTables<T> &g, const T *dens, int n, C2<T> *
   xa.out = pw;
   xa.dn = dens;
   xa.n_dn = n;
-  round_trip_poisson<T>(ctx, g, xa, n, u_out, acc, coef, 1.0);
+  round_trip_poisson<T>(ctx, g, xa, PoissonOut{n, coef, 1.0, tau_next}, u_out, acc, em1);
   CHECK_LAUNCH("poisson");
   return SBSE_OK;
 }
@@ -334,7 +343,7 @@ int poisson(sbse_ctx *ctx, const GridTables<T> &g, const T *dens, int n, C2<T> *
 // potentials of pair products prod[s] = (i1, j1, i2, j2) -> out (T) and/or acc (FP64, assigned)
 template <typename T>
 int poisson_products(sbse_ctx *ctx, const GridTables<T> &g, const T *orb, const int4 *prod_dev,
-                     int n_out, C2<T> *pw, T *u_out, double *acc) {
+                     int n_out, C2<T> *pw, T *u_out, T *acc) {
   const int S = (n_out + 1) / 2;
   XfwdArgs<T> xa{};
   xa.mode = XF_PACK_PROD;
@@ -342,7 +351,7 @@ int poisson_products(sbse_ctx *ctx, const GridTables<T> &g, const T *orb, const 
   xa.out = pw;
   xa.orb = orb;
   xa.prod = prod_dev;
-  round_trip_poisson<T>(ctx, g, xa, n_out, u_out, acc, 1.0, 0.0);
+  round_trip_poisson<T>(ctx, g, xa, PoissonOut{n_out, 1.0, 0.0, 0.0}, u_out, acc, nullptr);
   CHECK_LAUNCH("poisson_products");
   return SBSE_OK;
 }
@@ -383,6 +392,21 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   pw = (C *)vp;
   if ((rc = ensure(ctx, WS_WACC, (size_t)P * ng * sizeof(double), &vp))) return rc;
   wacc = (double *)vp;
+  // the damped time integral of Eq. (13) is summed in working precision and folded into the FP64
+  // accumulator every kFlush steps (FP64 arithmetic is ~70x slower than FP32 on this GPU)
+  constexpr int kFlush = 16;
+  T *accT = (T *)wacc;
+  if (sizeof(T) != sizeof(double)) {
+    if ((rc = ensure(ctx, WS_ACC32, (size_t)P * ng * sizeof(T), &vp))) return rc;
+    accT = (T *)vp;
+    CK(cudaMemsetAsync(accT, 0, (size_t)P * ng * sizeof(T), st));
+  }
+  C *em1 = nullptr;
+  if (p->feedback) {
+    if ((rc = ensure(ctx, WS_EM1, (size_t)P * ng * sizeof(C), &vp))) return rc;
+    em1 = (C *)vp;
+    CK(cudaMemsetAsync(em1, 0, (size_t)P * ng * sizeof(C), st));
+  }
   if ((rc = ensure(ctx, WS_N0, (size_t)L * sizeof(double), &vp))) return rc;
   n0 = (double *)vp;
   const long long nblk = (ng + 255) / 256;
@@ -445,10 +469,9 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw, st);
       launch_density<T>(g, acur, d, P, L, dn, st);
       CHECK_LAUNCH("clean");
-      if ((rc = poisson<T>(ctx, g, dn, P, pw, u, wacc, wts[n]))) return rc;
+      if ((rc = poisson<T>(ctx, g, dn, P, pw, u, accT, wts[n], em1, 0.5 * p->dt))) return rc;
       clk_end(ctx, ck);
     }
-    const T tau = (T)(pending ? p->dt : 0.5 * p->dt);
     size_t c0 = 0;
     clk_begin(ctx, 0, &c0);
     XfwdArgs<T> xa{};
@@ -456,7 +479,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     xa.n_items = L;
     xa.in = acur;
     xa.out = anext;
-    xa.tau = tau;
+    xa.pv = pending ? g.pv_dt : g.pv_half;
     round_trip_orbitals<T>(ctx, g, xa, anext, L, nullptr, L, nullptr);
     XfwdArgs<T> xb{};
     xb.mode = XF_PHASE_PAIR;
@@ -464,19 +487,20 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     xb.in = d;
     xb.out = d;
     xb.a = acur;
-    xb.u = u;
+    xb.em1 = em1;
     xb.L = L;
-    xb.tau = tau;
-    xb.feedback = p->feedback;
+    xb.pv = pending ? g.pv_dt : g.pv_half;
     round_trip_orbitals<T>(ctx, g, xb, d, P * L, anext, L, dn);
     CHECK_LAUNCH("step");
     clk_end(ctx, c0);
     size_t c1 = 0;
     clk_begin(ctx, 1, &c1);
     const bool recomputed = (M > 0 && (n + 1) % M == 0 && n + 1 < Nt);
-    if ((rc = poisson<T>(ctx, g, dn, P, pw, u, recomputed ? nullptr : wacc,
-                         recomputed ? 0.0 : wts[n + 1])))
+    if ((rc = poisson<T>(ctx, g, dn, P, pw, u, recomputed ? nullptr : accT,
+                         recomputed ? 0.0 : wts[n + 1], recomputed ? nullptr : em1, p->dt)))
       return rc;
+    if (sizeof(T) != sizeof(double) && ((n + 1) % kFlush == 0 || n + 1 == Nt))
+      launch_flush_acc<T>(wacc, accT, (long long)P * ng, st);
     clk_end(ctx, c1);
     std::swap(acur, anext);
   }

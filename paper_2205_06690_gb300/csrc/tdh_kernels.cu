@@ -250,8 +250,8 @@ void launch_xinv_orb(const GridTables<T> &g, C2<T> *data, int n_items, const C2<
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    k_xinv_poisson(GView<T> g, const C2<T> *data, long long rows_total, int n_out, T *u_out,
-                   double *acc, double coef, double keep) {
+    k_xinv_poisson(GView<T> g, const C2<T> *data, long long rows_total, PoissonOut po, T *u_out,
+                   T *acc, C2<T> *em1_out) {
   using C = C2<T>;
   extern __shared__ unsigned char smem_raw[];
   const int N = g.N, ld = kTP + 1;
@@ -278,23 +278,24 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const long long k = 2 * slot + h;
-      if (k >= n_out) break;
+      if (k >= po.n_out) break;
       const T val = h ? v.y : v.x;
       if (u_out) u_out[k * g.ng + idx] = val;
       if (acc) {
-        double *w = acc + k * g.ng + idx;
-        *w = (keep != 0.0) ? (*w) * keep + coef * (double)val : coef * (double)val;
+        T *w = acc + k * g.ng + idx;
+        *w = (po.keep != 0.0) ? (*w) + (T)po.coef * val : (T)po.coef * val;
       }
+      if (em1_out) em1_out[k * g.ng + idx] = phase_em1<T>(val, (T)po.tau_next);
     }
   }
 }
 
 template <typename T>
-void launch_xinv_poisson(const GridTables<T> &g, C2<T> *data, int n_slots, int n_out, T *u_out,
-                         double *acc, double coef, double keep, cudaStream_t s) {
+void launch_xinv_poisson(const GridTables<T> &g, C2<T> *data, int n_slots, const PoissonOut &po,
+                         T *u_out, T *acc, C2<T> *em1_out, cudaStream_t s) {
   const long long rows = (long long)n_slots * g.N * g.N;
   k_xinv_poisson<T><<<(unsigned)((rows + kTP - 1) / kTP), kThreads, fft_smem<T>(g.N, kTP), s>>>(
-      view(g), data, rows, n_out, u_out, acc, coef, keep);
+      view(g), data, rows, po, u_out, acc, em1_out);
   count_launch(1);
 }
 
@@ -529,16 +530,23 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// c - 1 per column from the reduced sums (FP64, one thread per column)
+__global__ void k_cm1(int n_cols, int L, const double *sums /* [c][2], times dV */, const double *n0,
+                      double *cm1) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cols) return;
+  const double x = (sums[2 * c] + sums[2 * c + 1]) / n0[c % L];
+  const double sq = sqrt(1.0 + x);
+  cm1[c] = -x / (sq * (1.0 + sq));
+}
+
 template <typename T>
-__global__ void k_renorm(long long ng, C2<T> *d, const C2<T> *a, int n_cols, int L,
-                         const double *sums /* [c][2], times dV */, const double *n0) {
+__global__ void k_renorm(long long ng, C2<T> *d, const C2<T> *a, int n_cols, int L, const double *cm1v) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (r >= ng) return;
   const int ell = c % L;
-  const double x = (sums[2 * c] + sums[2 * c + 1]) / n0[ell];
-  const double sq = sqrt(1.0 + x);
-  const T cm1 = (T)(-x / (sq * (1.0 + sq)));
+  const T cm1 = (T)cm1v[c];
   C2<T> *dp = d + (long long)c * ng + r;
   const C2<T> a0 = a[(long long)ell * ng + r];
   C2<T> dv = *dp;
@@ -558,6 +566,7 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
   b += (size_t)(M * n_occ) * sizeof(double);           // overlaps
   b += (size_t)(ptb * n_cols * 2) * sizeof(double);    // norm partials
   b += (size_t)(n_cols * 2) * sizeof(double);          // norm sums
+  b += (size_t)n_cols * sizeof(double);                // c - 1 per column
   return b;
 }
 
@@ -575,6 +584,7 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
   double *ov = part + chunks * M * n_occ;
   double *npart = ov + (long long)M * n_occ;
   double *sums = npart + ptb * n_cols * 2;
+  double *cm1 = sums + (long long)n_cols * 2;
   dim3 grid((unsigned)chunks, (M + kGemmBM - 1) / kGemmBM, (n_occ + kGemmBN - 1) / kGemmBN);
   k_gemm_nt_part<T><<<grid, kGemmThreads, 0, s>>>(
       M, n_occ, g.ng, kc, LoadComplexRow<T>{reinterpret_cast<const T *>(d), g.ng},
@@ -583,12 +593,41 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
   dim3 g2((unsigned)ptb, (n_cols + kCleanCols - 1) / kCleanCols);
   k_clean_update<T><<<g2, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
   launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
+  k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
   dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
-  k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, sums, n0);
-  count_launch(3);
+  k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);
+  count_launch(4);
 }
 
 // ------------------------------------------------------------------------------------------
+
+// out = exp(-i V_loc tau) per grid point
+// (computed in FP64 from the FP64 potential, then rounded to T)
+template <typename T> __global__ void k_phase_table(const double *v, long long ng, double tau, C2<T> *out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ng) {
+    const double2 e = expmi<double>(v[i] * tau);
+    out[i] = C2<T>{(T)e.x, (T)e.y};
+  }
+}
+template <typename T>
+void launch_phase_table(const double *v64, long long ng, double tau, C2<T> *out, cudaStream_t s) {
+  k_phase_table<T><<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(v64, ng, tau, out);
+  count_launch(1);
+}
+
+// acc64 += acc; acc = 0  (FP32 partial sums of the time integral folded into the FP64 W)
+template <typename T> __global__ void k_flush_acc(double *acc64, T *acc, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    acc64[i] += (double)acc[i];
+    acc[i] = T(0);
+  }
+}
+template <typename T> void launch_flush_acc(double *acc64, T *acc, long long n, cudaStream_t s) {
+  if (n > 0) k_flush_acc<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc64, acc, n);
+  count_launch(1);
+}
 
 template <typename T> __global__ void k_convert(const double *src, T *dst, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -634,8 +673,10 @@ void init_fft_kernels() {
   template void launch_zpass<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t);           \
   template void launch_xinv_orb<T>(const GridTables<T> &, C2<T> *, int, const C2<T> *, int, T *,   \
                                    cudaStream_t);                                                  \
-  template void launch_xinv_poisson<T>(const GridTables<T> &, C2<T> *, int, int, T *, double *,    \
-                                       double, double, cudaStream_t);                              \
+  template void launch_xinv_poisson<T>(const GridTables<T> &, C2<T> *, int, const PoissonOut &,    \
+                                       T *, T *, C2<T> *, cudaStream_t);                           \
+  template void launch_phase_table<T>(const double *, long long, double, C2<T> *, cudaStream_t);  \
+  template void launch_flush_acc<T>(double *, T *, long long, cudaStream_t);                       \
   template void launch_init_a<T>(const GridTables<T> &, const double *, int, const double *, int,  \
                                  C2<T> *, double *, int *, cudaStream_t);                          \
   template void launch_kick<T>(const GridTables<T> &, const double *, int, const C2<T> *, int,     \
