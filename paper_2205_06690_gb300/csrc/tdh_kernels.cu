@@ -439,97 +439,6 @@ void launch_density(const GridTables<T> &g, const C2<T> *a, const C2<T> *d, int 
 // eta^alpha = eta0 + d to its initial norm N0: d <- c d + (c - 1) eta0, c = (1 + x)^-1/2,
 // x = (2 Re<eta0|d> + |d|^2) / N0, c - 1 = -x / (sqrt(1+x) (1 + sqrt(1+x))).
 
-template <typename T> struct LoadComplexRow {  // row m = 2c + part of the complex columns d_c
-  const T *d;
-  long long ng;
-  __device__ T operator()(int m, long long k) const { return d[2 * ((long long)(m >> 1) * ng + k) + (m & 1)]; }
-};
-template <typename T> struct LoadRow {
-  const T *x;
-  long long ng;
-  __device__ T operator()(int n, long long k) const { return x[(long long)n * ng + k]; }
-};
-
-constexpr int kCleanPts = 64, kCleanCols = 16, kCleanS = 32;
-
-// d_c -= sum_s O[c][s] phi_s on a tile of 64 points x 16 columns; partial sums of
-// 2 Re(conj(eta0) d) and |d|^2 per column for the renormalisation.
-template <typename T>
-__global__ void __launch_bounds__(256)
-    k_clean_update(long long ng, const T *phi, int n_occ, const double *ov /* [2c+h][s] */,
-                   C2<T> *d, const C2<T> *a, int n_cols, int L, double *npart) {
-  using C = C2<T>;
-  __shared__ T ph[kCleanS][kCleanPts];
-  __shared__ C os[kCleanCols][kCleanS + 1];
-  __shared__ double red[2][4][kCleanPts];
-  const int pt = threadIdx.x % kCleanPts;
-  const int grp = threadIdx.x / kCleanPts;  // 4 groups of 4 columns
-  const long long r0 = (long long)blockIdx.x * kCleanPts;
-  const int c0 = blockIdx.y * kCleanCols;
-  const long long r = r0 + pt;
-  C acc[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) acc[j] = C{T(0), T(0)};
-  for (int s0 = 0; s0 < n_occ; s0 += kCleanS) {
-    for (int l = threadIdx.x; l < kCleanS * kCleanPts; l += 256) {
-      const int ss = l / kCleanPts, pp = l % kCleanPts;
-      const int s = s0 + ss;
-      const long long rr = r0 + pp;
-      ph[ss][pp] = (s < n_occ && rr < ng) ? phi[(long long)s * ng + rr] : T(0);
-    }
-    for (int l = threadIdx.x; l < kCleanCols * kCleanS; l += 256) {
-      const int cc = l / kCleanS, ss = l % kCleanS;
-      const int c = c0 + cc, s = s0 + ss;
-      C v = C{T(0), T(0)};
-      if (c < n_cols && s < n_occ)
-        v = C{(T)ov[(long long)(2 * c) * n_occ + s], (T)ov[(long long)(2 * c + 1) * n_occ + s]};
-      os[cc][ss] = v;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int ss = 0; ss < kCleanS; ++ss) {
-      const T p = ph[ss][pt];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const C o = os[grp * 4 + j][ss];
-        acc[j].x += o.x * p;
-        acc[j].y += o.y * p;
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int c = c0 + grp * 4 + j;
-    double v1 = 0.0, v2 = 0.0;
-    if (c < n_cols && r < ng) {
-      C *dp = d + (long long)c * ng + r;
-      C dv = *dp;
-      dv.x -= acc[j].x;
-      dv.y -= acc[j].y;
-      *dp = dv;
-      const C a0 = a[(long long)(c % L) * ng + r];
-      v1 = 2.0 * ((double)a0.x * dv.x + (double)a0.y * dv.y);
-      v2 = (double)dv.x * dv.x + (double)dv.y * dv.y;
-    }
-    red[0][grp][pt] = v1;
-    red[1][grp][pt] = v2;
-    __syncthreads();
-    for (int w = kCleanPts / 2; w > 0; w >>= 1) {
-      if (pt < w) {
-        red[0][grp][pt] += red[0][grp][pt + w];
-        red[1][grp][pt] += red[1][grp][pt + w];
-      }
-      __syncthreads();
-    }
-    if (pt == 0 && c < n_cols) {
-      npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = red[0][grp][0];
-      npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = red[1][grp][0];
-    }
-    __syncthreads();
-  }
-}
-
 // c - 1 per column from the reduced sums (FP64, one thread per column)
 __global__ void k_cm1(int n_cols, int L, const double *sums /* [c][2], times dV */, const double *n0,
                       double *cm1) {
@@ -555,18 +464,178 @@ __global__ void k_renorm(long long ng, C2<T> *d, const C2<T> *a, int n_cols, int
   *dp = dv;
 }
 
+// Overlaps of the complex columns d_c with the occupied orbitals, split over chunks of grid
+// points: part[chunk][c][s] = sum_{r in chunk} (Re d_c(r), Im d_c(r)) phi_s(r). Tile of 64
+// columns x 64 states, 16 points per stage, 4 x 4 complex outputs per thread.
+constexpr int kOvC = 64, kOvS = 64, kOvK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_clean_overlap(const C2<T> *d, const T *phi, int n_cols, int n_occ, long long ng,
+                    long long kchunk, double *part) {
+  __shared__ __align__(16) T Dre[kOvK][kOvC + 4];
+  __shared__ __align__(16) T Dim[kOvK][kOvC + 4];
+  __shared__ __align__(16) T Ph[kOvK][kOvS + 4];
+  const int c0 = blockIdx.y * kOvC, s0 = blockIdx.z * kOvS;
+  const long long kbeg = (long long)blockIdx.x * kchunk;
+  const long long kend = (kbeg + kchunk < ng) ? kbeg + kchunk : ng;
+  const int tc = threadIdx.x % 16, ts = threadIdx.x / 16;
+  T are[4][4], aim[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) are[i][j] = aim[i][j] = T(0);
+  for (long long k0 = kbeg; k0 < kend; k0 += kOvK) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int l = threadIdx.x + it * 256;
+      const int cc = l / kOvK, kk = l % kOvK;
+      const long long k = k0 + kk;
+      const int c = c0 + cc, s = s0 + cc;
+      C2<T> v = C2<T>{T(0), T(0)};
+      if (c < n_cols && k < kend) v = d[(long long)c * ng + k];
+      Dre[kk][cc] = v.x;
+      Dim[kk][cc] = v.y;
+      Ph[kk][cc] = (s < n_occ && k < kend) ? phi[(long long)s * ng + k] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kOvK; ++kk) {
+      T xr[4], xi[4], p[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xr[i] = Dre[kk][tc * 4 + i];
+        xi[i] = Dim[kk][tc * 4 + i];
+        p[i] = Ph[kk][ts * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          are[i][j] += xr[i] * p[j];
+          aim[i][j] += xi[i] * p[j];
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int c = c0 + tc * 4 + i;
+    if (c >= n_cols) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int s = s0 + ts * 4 + j;
+      if (s >= n_occ) continue;
+      double *o = part + (((long long)blockIdx.x * n_cols + c) * n_occ + s) * 2;
+      o[0] = (double)are[i][j];
+      o[1] = (double)aim[i][j];
+    }
+  }
+}
+
+// d_c(r) -= sum_s O[c][s] phi_s(r) on 128 points per block, all columns in groups of 32 (4 points
+// x 4 columns per thread), plus per-block partial sums of 2 Re(conj(eta0) d) and |d|^2 per column.
+constexpr int kUpPts = 128, kUpCols = 32, kUpS = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_clean_update2(long long ng, const T *phi, int n_occ, const double *ov /* [c][s][2], x dV */,
+                    C2<T> *d, const C2<T> *a, int n_cols, int L, double *npart) {
+  using C = C2<T>;
+  __shared__ __align__(16) T Ph[kUpS][kUpPts];
+  __shared__ __align__(16) C Os[kUpCols][kUpS + 1];
+  const int tp = threadIdx.x % 32, tcg = threadIdx.x / 32;
+  const long long r0 = (long long)blockIdx.x * kUpPts;
+  const bool one_tile = n_occ <= kUpS;
+  auto load_phi = [&](int st0) {
+    for (int l = threadIdx.x; l < kUpS * kUpPts; l += 256) {
+      const int ss = l / kUpPts, pp = l % kUpPts;
+      const int s = st0 + ss;
+      const long long r = r0 + pp;
+      Ph[ss][pp] = (s < n_occ && r < ng) ? phi[(long long)s * ng + r] : T(0);
+    }
+  };
+  if (one_tile) load_phi(0);
+  for (int cg0 = 0; cg0 < n_cols; cg0 += kUpCols) {
+    C acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = C{T(0), T(0)};
+    for (int st0 = 0; st0 < n_occ; st0 += kUpS) {
+      __syncthreads();
+      if (!one_tile) load_phi(st0);
+      for (int l = threadIdx.x; l < kUpCols * kUpS; l += 256) {
+        const int cc = l / kUpS, ss = l % kUpS;
+        const int c = cg0 + cc, s = st0 + ss;
+        C v = C{T(0), T(0)};
+        if (c < n_cols && s < n_occ) {
+          const double *o = ov + ((long long)c * n_occ + s) * 2;
+          v = C{(T)o[0], (T)o[1]};
+        }
+        Os[cc][ss] = v;
+      }
+      __syncthreads();
+      const int smax = (n_occ - st0) < kUpS ? (n_occ - st0) : kUpS;
+      for (int ss = 0; ss < smax; ++ss) {
+        T p[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) p[j] = Ph[ss][tp * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const C o = Os[tcg * 4 + i][ss];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j].x += o.x * p[j];
+            acc[i][j].y += o.y * p[j];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int c = cg0 + tcg * 4 + i;
+      double v1 = 0.0, v2 = 0.0;
+      if (c < n_cols) {
+        C *dp = d + (long long)c * ng + r0 + tp * 4;
+        const C *ap = a + (long long)(c % L) * ng + r0 + tp * 4;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (r0 + tp * 4 + j < ng) {
+            C dv = dp[j];
+            dv.x -= acc[i][j].x;
+            dv.y -= acc[i][j].y;
+            dp[j] = dv;
+            const C a0 = ap[j];
+            v1 += 2.0 * ((double)a0.x * dv.x + (double)a0.y * dv.y);
+            v2 += (double)dv.x * dv.x + (double)dv.y * dv.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+      }
+      if (tp == 0 && c < n_cols) {
+        npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = v1;
+        npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = v2;
+      }
+    }
+  }
+}
+
 template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L) {
   const long long n_cols = (long long)P * L;
-  const long long M = 2 * n_cols;
   const long long kc = gemm_kchunk(ng);
   const long long chunks = (ng + kc - 1) / kc;
-  const long long ptb = (ng + kCleanPts - 1) / kCleanPts;
+  const long long ptb = (ng + kUpPts - 1) / kUpPts;
   size_t b = 0;
-  b += (size_t)(chunks * M * n_occ) * sizeof(double);  // overlap partials
-  b += (size_t)(M * n_occ) * sizeof(double);           // overlaps
-  b += (size_t)(ptb * n_cols * 2) * sizeof(double);    // norm partials
-  b += (size_t)(n_cols * 2) * sizeof(double);          // norm sums
-  b += (size_t)n_cols * sizeof(double);                // c - 1 per column
+  b += (size_t)(chunks * n_cols * n_occ * 2) * sizeof(double);  // overlap partials
+  b += (size_t)(n_cols * n_occ * 2) * sizeof(double);           // overlaps
+  b += (size_t)(ptb * n_cols * 2) * sizeof(double);             // norm partials
+  b += (size_t)(n_cols * 2) * sizeof(double);                   // norm sums
+  b += (size_t)n_cols * sizeof(double);                         // c - 1 per column
   return b;
 }
 
@@ -576,27 +645,24 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
                   cudaStream_t s) {
   (void)work_bytes;
   const int n_cols = P * L;
-  const int M = 2 * n_cols;
   const long long kc = gemm_kchunk(g.ng);
   const long long chunks = (g.ng + kc - 1) / kc;
-  const long long ptb = (g.ng + kCleanPts - 1) / kCleanPts;
+  const long long ptb = (g.ng + kUpPts - 1) / kUpPts;
   double *part = work;
-  double *ov = part + chunks * M * n_occ;
-  double *npart = ov + (long long)M * n_occ;
+  double *ov = part + chunks * n_cols * n_occ * 2;
+  double *npart = ov + (long long)n_cols * n_occ * 2;
   double *sums = npart + ptb * n_cols * 2;
   double *cm1 = sums + (long long)n_cols * 2;
-  dim3 grid((unsigned)chunks, (M + kGemmBM - 1) / kGemmBM, (n_occ + kGemmBN - 1) / kGemmBN);
-  k_gemm_nt_part<T><<<grid, kGemmThreads, 0, s>>>(
-      M, n_occ, g.ng, kc, LoadComplexRow<T>{reinterpret_cast<const T *>(d), g.ng},
-      LoadRow<T>{phi_occ, g.ng}, part);
-  launch_reduce_cols(part, (int)chunks, M * n_occ, dV, ov, s);
-  dim3 g2((unsigned)ptb, (n_cols + kCleanCols - 1) / kCleanCols);
-  k_clean_update<T><<<g2, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
+  dim3 grid((unsigned)chunks, (n_cols + kOvC - 1) / kOvC, (n_occ + kOvS - 1) / kOvS);
+  k_clean_overlap<T><<<grid, 256, 0, s>>>(d, phi_occ, n_cols, n_occ, g.ng, kc, part);
+  count_launch(1);
+  launch_reduce_cols(part, (int)chunks, n_cols * n_occ * 2, dV, ov, s);
+  k_clean_update2<T><<<(unsigned)ptb, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
   launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
   k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
   dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
   k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);
-  count_launch(4);
+  count_launch(3);
 }
 
 // ------------------------------------------------------------------------------------------
