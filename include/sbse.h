@@ -145,8 +145,27 @@ int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out);
  * Requires sbse_build_A. Errors: INVALID_ARG, NOT_READY, UNSUPPORTED, CUDA. */
 int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs);
 
+/* Allocation-free variant of sbse_spectrum, for callers that cannot allocate device memory (for
+ * example a host framework whose memory pool has reserved the whole GPU, or code that must not
+ * trigger an allocation once it runs). The paper has no counterpart: it is an interface addition.
+ * It computes the lowest k eigenvalues of the real symmetric n x n matrix at a_dev (device pointer,
+ * FP64, row-major, not modified) into evals_dev (device pointer, k doubles, ascending) with the
+ * same kernels as sbse_spectrum, on `stream` (a cudaStream_t; NULL = default stream), and
+ * returns after the stream has synchronised. It calls no cudaMalloc, cudaFree or allocating
+ * library routine: its scratch (n^2 + 2n doubles) is a fixed device array of
+ * SBSE_NOALLOC_MAX_N^2 + 2 SBSE_NOALLOC_MAX_N doubles (about 2 MB) that every GPU loading the
+ * library holds until the process exits. The first call on a device resolves that array's device
+ * address (once per device, on the current device); make that first call before any stream
+ * capture. All calls on a device share the array, so calls that overlap on the GPU race; the
+ * array keeps the last call's contents, and nothing in it needs to start at zero.
+ * Errors: INVALID_ARG (null pointer, k outside 1..n), SHAPE (n > SBSE_NOALLOC_MAX_N), CUDA;
+ * the message is available from sbse_last_error(NULL). */
+#define SBSE_NOALLOC_MAX_N 512
+int sbse_spectrum_noalloc(const double *a_dev, int n, int k, double *evals_dev, void *stream);
+
 /* Message of the last failed call on ctx ("" if none). The pointer stays valid until the next
- * call on ctx. ctx may be NULL (message of the last failed sbse_create on this thread). */
+ * call on ctx. ctx may be NULL: message of the last failed context-free call on this thread
+ * (sbse_create, sbse_spectrum_noalloc). */
 const char *sbse_last_error(const sbse_ctx *ctx);
 
 /* The CUDA stream (cudaStream_t) all device work of ctx is issued on, for event timing by the

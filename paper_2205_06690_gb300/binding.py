@@ -90,6 +90,7 @@ def load() -> C.CDLL:
         "sbse_get_stream": (i, [vp, C.POINTER(vp)]),
         "sbse_profile": (i, [vp, i]),
         "sbse_kernel_launches": (i, [C.POINTER(C.c_longlong)]),
+        "sbse_spectrum_noalloc": (i, [vp, i, i, vp, vp]),
         "sbse_phase_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
     }
     for name, (res, args) in sig.items():
@@ -194,6 +195,12 @@ def sbse_kernel_launches() -> int:
     n = C.c_longlong()
     _check(None, load().sbse_kernel_launches(C.byref(n)))
     return n.value
+
+
+def sbse_spectrum_noalloc(a_dev: int, n: int, k: int, evals_dev: int, stream: int = 0) -> None:
+    """Allocation-free eigenvalues: device pointers in and out (see include/sbse.h)."""
+    _check(None, load().sbse_spectrum_noalloc(C.c_void_p(a_dev), n, k, C.c_void_p(evals_dev),
+                                              C.c_void_p(stream)))
 
 
 def sbse_profile(ctx, enable: bool) -> None:

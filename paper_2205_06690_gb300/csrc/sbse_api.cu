@@ -14,8 +14,13 @@
 #include "kernels.h"
 #include "sbse.h"
 
+namespace {
+thread_local std::string g_create_error;
+}
+
 namespace sbse {
 void init_fft_kernels();
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }
@@ -23,8 +28,6 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 using namespace sbse;
 
 namespace {
-
-thread_local std::string g_create_error;
 
 struct DevBuf {
   void *p = nullptr;
