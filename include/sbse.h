@@ -172,6 +172,12 @@ const char *sbse_last_error(const sbse_ctx *ctx);
  * caller. Errors: INVALID_ARG. */
 int sbse_get_stream(const sbse_ctx *ctx, void **stream);
 
+/* Options. SBSE_OPT_TENSOR_CORES (default 1): in SBSE_MIXED, run the grid-sum contractions of
+ * sbse_build_A on the tensor cores (tcgen05, BF16 high/low split of both operands, three products
+ * per term, FP32 accumulation); 0 uses FP32 CUDA-core arithmetic. Errors: INVALID_ARG. */
+#define SBSE_OPT_TENSOR_CORES 1
+int sbse_set_option(sbse_ctx *ctx, int option, int value);
+
 /* Number of CUDA kernel launches the library has issued in this process (all contexts), for
  * counting the kernels inside a timed region. Errors: INVALID_ARG. */
 int sbse_kernel_launches(long long *count);

@@ -32,6 +32,7 @@ SBSE_COEFF_GAUSSIAN = 0
 SBSE_COEFF_SIGN = 1
 SBSE_EXCHANGE = 1
 SBSE_DIRECT = 2
+SBSE_OPT_TENSOR_CORES = 1
 
 _ERR_NAMES = {v: k for k, v in globals().items() if k.startswith("SBSE_ERR_")}
 
@@ -90,6 +91,7 @@ def load() -> C.CDLL:
         "sbse_get_stream": (i, [vp, C.POINTER(vp)]),
         "sbse_profile": (i, [vp, i]),
         "sbse_kernel_launches": (i, [C.POINTER(C.c_longlong)]),
+        "sbse_set_option": (i, [vp, i, i]),
         "sbse_spectrum_noalloc": (i, [vp, i, i, vp, vp]),
         "sbse_phase_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
     }
@@ -189,6 +191,10 @@ def sbse_get_stream(ctx) -> int:
     s = C.c_void_p()
     _check(ctx, load().sbse_get_stream(ctx, C.byref(s)))
     return int(s.value or 0)
+
+
+def sbse_set_option(ctx, option: int, value: int) -> None:
+    _check(ctx, load().sbse_set_option(ctx, option, value))
 
 
 def sbse_kernel_launches() -> int:

@@ -99,9 +99,11 @@ template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C
 template <typename T> void launch_density(const GridTables<T> &g, const C2<T> *a, const C2<T> *d,
                                           int P, int L, T *dens, cudaStream_t s);
 // cleaning of Eq. (15): overlaps O[c][s] = dV sum_r phi_s d_c (c < P*L complex columns)
+// use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait
 template <typename T> void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
                                         const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
-                                        double dV, double *work, size_t work_bytes, cudaStream_t s);
+                                        double dV, double *work, size_t work_bytes, bool use_tc,
+                                        int *err, cudaStream_t s);
 template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L);
 // d64 -> T conversion and FP64 -> T copies
 template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s);
@@ -115,6 +117,16 @@ template <typename T> void launch_prod_gemm(const T *F, const int2 *xi, int M, c
 template <typename T> size_t prod_gemm_work_bytes(int M, int Nn, long long ng);
 void launch_assemble_A(const double *eps_o, const double *eps_c, int n_o, int n_c, double scissor,
                        const double *K, const double *Dab, int P, double *A, cudaStream_t s);
+
+// tensor-core (tcgen05, BF16 split, FP32 accumulate) version of launch_prod_gemm for FP32 inputs;
+// *err (device int) is set when a bounded wait on the tensor cores times out
+int launch_umma_prod_gemm(const float *F, const int2 *xi, int M, const float *Y, int Nn, long long ng,
+                          double scale, double *out, double *work, int *err, cudaStream_t s);
+size_t umma_prod_gemm_work_bytes(int M, int Nn, long long ng);
+// cleaning overlaps on the tensor cores: out[2c + h][s] = scale sum_r (Re, Im)_h d_c phi_s
+int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const float *phi, int n_occ,
+                              long long ng, double scale, double *out, double *work, int *err,
+                              cudaStream_t s);
 
 // ---- eigensolver (eig.cu)
 int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, cudaStream_t s);

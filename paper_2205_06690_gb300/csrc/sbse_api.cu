@@ -70,6 +70,8 @@ struct sbse_ctx {
   // scratch
   DevBuf ws[24];
   int *flag = nullptr;
+  // mixed mode: grid-sum contractions on the tensor cores (SBSE_OPT_TENSOR_CORES)
+  int tensor_cores = 1;
   // profiling
   bool prof = false;
   PhaseClock clk;
@@ -423,6 +425,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   if ((rc = ensure(ctx, WS_IDX, (size_t)S * sizeof(int4), &vp))) return rc;
   prod = (int4 *)vp;
 
+  CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), st));
   // ---- init: eta0_l (Eq. 14), N0_l, q_ij (FP64), kick
   CK(cudaMemcpyAsync(coef, coef_host.data(), coef_host.size() * sizeof(double),
                      cudaMemcpyHostToDevice, st));
@@ -469,7 +472,8 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       clk_begin(ctx, 2, &ck);
       if (pending) launch_half_phase<T>(g, acur, d, u, P, L, (T)(0.5 * p->dt), p->feedback, st);
       pending = false;
-      launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw, st);
+      launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
+                      ctx->tensor_cores != 0, ctx->flag, st);
       launch_density<T>(g, acur, d, P, L, dn, st);
       CHECK_LAUNCH("clean");
       if ((rc = poisson<T>(ctx, g, dn, P, pw, u, accT, wts[n], em1, 0.5 * p->dt))) return rc;
@@ -507,11 +511,43 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     clk_end(ctx, c1);
     std::swap(acur, anext);
   }
+  {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h) return fail(ctx, SBSE_ERR_DEVICE_TIMEOUT, "cleaning overlaps: wait on the tensor cores timed out");
+  }
   // results into the canonical slots
   for (int k = 0; k < P; ++k)
     CK(cudaMemcpyAsync(ctx->W + (long long)slots[k] * ng, wacc + (long long)k * ng,
                        ng * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
+  return SBSE_OK;
+}
+
+// out[m][n] = dV sum_r phi_xi[m].x phi_xi[m].y (r) Y_n(r): on the tensor cores (tcgen05, BF16 split,
+// FP32 accumulation) in the mixed mode, in FP64 SIMT in the FP64 mode
+template <typename T>
+int contract(sbse_ctx *ctx, const int2 *xi_dev, int M, const T *Y, int Nn, double *out) {
+  void *vp;
+  int rc;
+  cudaStream_t st = ctx->stream;
+  if (sizeof(T) == sizeof(float) && ctx->tensor_cores) {
+    const size_t gw = umma_prod_gemm_work_bytes(M, Nn, ctx->ng);
+    if ((rc = ensure(ctx, WS_GEMM, gw, &vp))) return rc;
+    CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), st));
+    launch_umma_prod_gemm((const float *)phi_T<T>(ctx), xi_dev, M, (const float *)Y, Nn, ctx->ng,
+                          ctx->dV, out, (double *)vp, ctx->flag, st);
+    CHECK_LAUNCH("tensor-core contraction");
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h) return fail(ctx, SBSE_ERR_DEVICE_TIMEOUT, "tensor-core contraction: wait on the MMA timed out");
+    return SBSE_OK;
+  }
+  const size_t gw = prod_gemm_work_bytes<T>(M, Nn, ctx->ng);
+  if ((rc = ensure(ctx, WS_GEMM, gw, &vp))) return rc;
+  launch_prod_gemm<T>(phi_T<T>(ctx), xi_dev, M, Y, Nn, ctx->ng, ctx->dV, out, (double *)vp, gw, st);
   return SBSE_OK;
 }
 
@@ -558,9 +594,7 @@ template <typename T> int run_build_A(sbse_ctx *ctx, unsigned terms) {
     CK(cudaMemcpyAsync(xi_dev, xi.data(), n * sizeof(int2), cudaMemcpyHostToDevice, st));
     if ((rc = ensure(ctx, WS_K, (size_t)n * n * sizeof(double), &vp))) return rc;
     K = (double *)vp;
-    const size_t gw = prod_gemm_work_bytes<T>(n, n, ng);
-    if ((rc = ensure(ctx, WS_GEMM, gw, &vp))) return rc;
-    launch_prod_gemm<T>(phi_T<T>(ctx), xi_dev, n, U, n, ng, ctx->dV, K, (double *)vp, gw, st);
+    if ((rc = contract<T>(ctx, xi_dev, n, U, n, K))) return rc;
     CHECK_LAUNCH("exchange");
     CK(cudaStreamSynchronize(st));
   }
@@ -583,9 +617,7 @@ template <typename T> int run_build_A(sbse_ctx *ctx, unsigned terms) {
     }
     if ((rc = ensure(ctx, WS_DAB, (size_t)Mab * P * sizeof(double), &vp))) return rc;
     Dab = (double *)vp;
-    const size_t gw = prod_gemm_work_bytes<T>(Mab, P, ng);
-    if ((rc = ensure(ctx, WS_GEMM, gw, &vp))) return rc;
-    launch_prod_gemm<T>(phi_T<T>(ctx), xi_dev, Mab, Wt, P, ng, ctx->dV, Dab, (double *)vp, gw, st);
+    if ((rc = contract<T>(ctx, xi_dev, Mab, Wt, P, Dab))) return rc;
     CHECK_LAUNCH("direct");
   }
   clk_end(ctx, c3);
@@ -848,6 +880,15 @@ int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs) {
   for (int i = 0; i < k; ++i)
     if (!isfinite(evals[i])) return fail(ctx, SBSE_ERR_NUMERIC, "eigenvalue is not finite");
   return SBSE_OK;
+}
+
+int sbse_set_option(sbse_ctx *ctx, int option, int value) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  if (option == SBSE_OPT_TENSOR_CORES) {
+    ctx->tensor_cores = value != 0;
+    return SBSE_OK;
+  }
+  return fail(ctx, SBSE_ERR_INVALID_ARG, "unknown option");
 }
 
 int sbse_kernel_launches(long long *count) {

@@ -526,9 +526,9 @@ __global__ void __launch_bounds__(256)
     for (int j = 0; j < 4; ++j) {
       const int s = s0 + ts * 4 + j;
       if (s >= n_occ) continue;
-      double *o = part + (((long long)blockIdx.x * n_cols + c) * n_occ + s) * 2;
+      double *o = part + ((long long)blockIdx.x * 2 * n_cols + 2 * c) * n_occ + s;
       o[0] = (double)are[i][j];
-      o[1] = (double)aim[i][j];
+      o[n_occ] = (double)aim[i][j];
     }
   }
 }
@@ -539,7 +539,7 @@ constexpr int kUpPts = 128, kUpCols = 32, kUpS = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_clean_update2(long long ng, const T *phi, int n_occ, const double *ov /* [c][s][2], x dV */,
+    k_clean_update2(long long ng, const T *phi, int n_occ, const double *ov /* [2c+h][s], x dV */,
                     C2<T> *d, const C2<T> *a, int n_cols, int L, double *npart) {
   using C = C2<T>;
   __shared__ __align__(16) T Ph[kUpS][kUpPts];
@@ -570,8 +570,8 @@ __global__ void __launch_bounds__(256)
         const int c = cg0 + cc, s = st0 + ss;
         C v = C{T(0), T(0)};
         if (c < n_cols && s < n_occ) {
-          const double *o = ov + ((long long)c * n_occ + s) * 2;
-          v = C{(T)o[0], (T)o[1]};
+          const double *o = ov + (long long)(2 * c) * n_occ + s;
+          v = C{(T)o[0], (T)o[n_occ]};
         }
         Os[cc][ss] = v;
       }
@@ -631,7 +631,9 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
   const long long chunks = (ng + kc - 1) / kc;
   const long long ptb = (ng + kUpPts - 1) / kUpPts;
   size_t b = 0;
-  b += (size_t)(chunks * n_cols * n_occ * 2) * sizeof(double);  // overlap partials
+  const size_t tc_part = umma_prod_gemm_work_bytes((int)(2 * n_cols), n_occ, ng);
+  const size_t simt_part = (size_t)(chunks * n_cols * n_occ * 2) * sizeof(double);
+  b += simt_part > tc_part ? simt_part : tc_part;                 // overlap partials
   b += (size_t)(n_cols * n_occ * 2) * sizeof(double);           // overlaps
   b += (size_t)(ptb * n_cols * 2) * sizeof(double);             // norm partials
   b += (size_t)(n_cols * 2) * sizeof(double);                   // norm sums
@@ -642,21 +644,28 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
 template <typename T>
 void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
                   int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
-                  cudaStream_t s) {
+                  bool use_tc, int *err, cudaStream_t s) {
   (void)work_bytes;
   const int n_cols = P * L;
   const long long kc = gemm_kchunk(g.ng);
   const long long chunks = (g.ng + kc - 1) / kc;
   const long long ptb = (g.ng + kUpPts - 1) / kUpPts;
   double *part = work;
-  double *ov = part + chunks * n_cols * n_occ * 2;
+  const size_t tc_part = umma_prod_gemm_work_bytes(2 * n_cols, n_occ, g.ng) / sizeof(double);
+  const size_t simt_part = (size_t)(chunks * n_cols * n_occ * 2);
+  double *ov = part + (simt_part > tc_part ? simt_part : tc_part);
   double *npart = ov + (long long)n_cols * n_occ * 2;
   double *sums = npart + ptb * n_cols * 2;
   double *cm1 = sums + (long long)n_cols * 2;
-  dim3 grid((unsigned)chunks, (n_cols + kOvC - 1) / kOvC, (n_occ + kOvS - 1) / kOvS);
-  k_clean_overlap<T><<<grid, 256, 0, s>>>(d, phi_occ, n_cols, n_occ, g.ng, kc, part);
-  count_launch(1);
-  launch_reduce_cols(part, (int)chunks, n_cols * n_occ * 2, dV, ov, s);
+  if (use_tc && sizeof(T) == sizeof(float)) {
+    launch_umma_clean_overlap(reinterpret_cast<const float *>(d), n_cols,
+                              reinterpret_cast<const float *>(phi_occ), n_occ, g.ng, dV, ov, part, err, s);
+  } else {
+    dim3 grid((unsigned)chunks, (n_cols + kOvC - 1) / kOvC, (n_occ + kOvS - 1) / kOvS);
+    k_clean_overlap<T><<<grid, 256, 0, s>>>(d, phi_occ, n_cols, n_occ, g.ng, kc, part);
+    count_launch(1);
+    launch_reduce_cols(part, (int)chunks, n_cols * n_occ * 2, dV, ov, s);
+  }
   k_clean_update2<T><<<(unsigned)ptb, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
   launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
   k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
@@ -752,7 +761,8 @@ void init_fft_kernels() {
   template void launch_density<T>(const GridTables<T> &, const C2<T> *, const C2<T> *, int, int,   \
                                   T *, cudaStream_t);                                              \
   template void launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *, C2<T> *,     \
-                                int, int, const double *, double, double *, size_t, cudaStream_t); \
+                                int, int, const double *, double, double *, size_t, bool, int *,   \
+                                cudaStream_t);                                                     \
   template size_t clean_work_bytes<T>(long long, int, int, int);                                   \
   template void launch_convert<T>(const double *, T *, long long, cudaStream_t);
 

@@ -1,0 +1,342 @@
+// Grid-sum contractions of Eq. (1) on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   part[chunk][m][n] = sum_{r in chunk} X_m(r) Y_n(r),  X_m = F[i1(m)] F[i2(m)],  Y_n = Y[n]
+//
+// The pair products X (phi_i phi_a for the exchange element, phi_a phi_b for the direct element) are
+// formed by the producer warps from FP32 orbitals and never stored in global memory. Both operands
+// are split into BF16 high and low parts (x = hi + lo) and three MMAs per K slice accumulate
+// hi*hi + hi*lo + lo*hi in FP32 in tensor memory (relative error ~1e-5 of each product instead of
+// BF16's 4e-3). One CTA owns a 128 x NT output tile (NT <= 256, multiple of 16) and a chunk of grid
+// points; stages of 64 points are double-buffered in shared memory in the canonical K-major layout
+// without swizzle (8-row x 16-byte core matrices: K-adjacent core matrices 128 B apart, row groups
+// 1024 B apart). Thread 0 issues the MMAs and commits them to one mbarrier per stage; every wait on
+// an mbarrier is bounded and sets *err on timeout. Partials (FP64) are reduced by the caller.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace sbse {
+
+constexpr int kUmM = 128;     // rows per tile (UMMA M)
+constexpr int kUmBK = 64;     // grid points per stage
+constexpr int kUmThreads = 128;
+constexpr int kUmStages = 2;
+constexpr unsigned kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared memory matrix descriptor: start >> 4 [0,14), LBO >> 4 [16,30), SBO >> 4 [32,46),
+// version 1 [46,48), base offset 0, layout SWIZZLE_NONE (0) [61,64)
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1), B BF16
+// (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t make_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (unsigned i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+
+// bytes of one stage: A hi/lo (128 rows) + B hi/lo (NT rows), BF16, 64 points
+__host__ __device__ constexpr size_t umma_stage_bytes(int nt) {
+  return (size_t)2 * (kUmM + nt) * kUmBK * 2;
+}
+
+// offset (bytes) of element (row, k) of a R x 64 BF16 tile in the canonical no-swizzle K-major layout
+__device__ __forceinline__ uint32_t canon_off(int row, int kc) {
+  return (uint32_t)(((row >> 3) * 8 + kc) * 128 + (row & 7) * 16);
+}
+
+__device__ __forceinline__ void split8(const float *x, uint4 *hi, uint4 *lo) {
+  __nv_bfloat162 h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
+    h[i] = __halves2bfloat162(h0, h1);
+    l[i] = __halves2bfloat162(l0, l1);
+  }
+  *hi = *reinterpret_cast<uint4 *>(h);
+  *lo = *reinterpret_cast<uint4 *>(l);
+}
+
+// A-operand modes: pair products X_m = F[xi[m].x] F[xi[m].y], or the real / imaginary parts of
+// complex rows (row m = 2c + h of the interleaved complex array F, c < M / 2)
+enum UmmaAMode { UA_PRODUCT = 0, UA_COMPLEX = 1 };
+
+// Producer: fill one stage. A unit = 8 rows x 32 points (4 core matrices along K); lane l covers
+// row (l & 7) of the group and core matrix kq = l >> 3, i.e. 8 consecutive points of one row.
+template <int AMODE>
+__device__ __forceinline__ void produce_stage(uint8_t *st, int nt, const float *F, const int2 *xi, int M,
+                                              int m0, const float *Y, int Nn, int n0, long long ng,
+                                              long long k0, long long kend) {
+  uint8_t *a_hi = st;
+  uint8_t *a_lo = a_hi + kUmM * kUmBK * 2;
+  uint8_t *b_hi = a_lo + kUmM * kUmBK * 2;
+  uint8_t *b_lo = b_hi + nt * kUmBK * 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rr = lane & 7, kq = lane >> 3;
+  const int units_a = (kUmM / 8) * 2, units_b = (nt / 8) * 2;
+  const bool vec_ok = (ng & 3) == 0;  // 16-byte aligned rows
+  for (int u = warp; u < units_a + units_b; u += kUmThreads / 32) {
+    const bool isA = u < units_a;
+    const int uu = isA ? u : u - units_a;
+    const int row = (uu >> 1) * 8 + rr;
+    const int kc = (uu & 1) * 4 + kq;  // core matrix index along K (0..7)
+    const long long kb = k0 + kc * 8;
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = 0.f;
+    const bool full = vec_ok && kb + 8 <= kend;
+    if (isA && AMODE == UA_COMPLEX) {
+      const int m = m0 + row;
+      if (m < M) {
+        const float *f = F + 2 * ((long long)(m >> 1) * ng + kb) + (m & 1);
+        if (full) {
+          const float4 c0 = *reinterpret_cast<const float4 *>(f - (m & 1));
+          const float4 c1 = *reinterpret_cast<const float4 *>(f - (m & 1) + 4);
+          const float4 c2 = *reinterpret_cast<const float4 *>(f - (m & 1) + 8);
+          const float4 c3 = *reinterpret_cast<const float4 *>(f - (m & 1) + 12);
+          if (m & 1) {
+            x[0] = c0.y; x[1] = c0.w; x[2] = c1.y; x[3] = c1.w; x[4] = c2.y; x[5] = c2.w; x[6] = c3.y; x[7] = c3.w;
+          } else {
+            x[0] = c0.x; x[1] = c0.z; x[2] = c1.x; x[3] = c1.z; x[4] = c2.x; x[5] = c2.z; x[6] = c3.x; x[7] = c3.z;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? f[2 * j] : 0.f;
+        }
+      }
+    } else if (isA) {
+      const int m = m0 + row;
+      if (m < M) {
+        const int2 q = xi[m];
+        const float *f1 = F + (long long)q.x * ng + kb, *f2 = F + (long long)q.y * ng + kb;
+        if (full) {
+          const float4 a0 = *reinterpret_cast<const float4 *>(f1), a1 = *reinterpret_cast<const float4 *>(f1 + 4);
+          const float4 b0 = *reinterpret_cast<const float4 *>(f2), b1 = *reinterpret_cast<const float4 *>(f2 + 4);
+          x[0] = a0.x * b0.x; x[1] = a0.y * b0.y; x[2] = a0.z * b0.z; x[3] = a0.w * b0.w;
+          x[4] = a1.x * b1.x; x[5] = a1.y * b1.y; x[6] = a1.z * b1.z; x[7] = a1.w * b1.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? f1[j] * f2[j] : 0.f;
+        }
+      }
+    } else {
+      const int n = n0 + row;
+      if (n < Nn) {
+        const float *y = Y + (long long)n * ng + kb;
+        if (full) {
+          const float4 a0 = *reinterpret_cast<const float4 *>(y), a1 = *reinterpret_cast<const float4 *>(y + 4);
+          x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+          x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? y[j] : 0.f;
+        }
+      }
+    }
+    uint4 hi, lo;
+    split8(x, &hi, &lo);
+    const uint32_t off = canon_off(row, kc);
+    *reinterpret_cast<uint4 *>((isA ? a_hi : b_hi) + off) = hi;
+    *reinterpret_cast<uint4 *>((isA ? a_lo : b_lo) + off) = lo;
+  }
+}
+
+template <int AMODE>
+__global__ void __launch_bounds__(kUmThreads)
+    k_umma_prod_gemm(const float *F, const int2 *xi, int M, const float *Y, int Nn, int nt, long long ng,
+                     long long kchunk, double *part, int *err) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t mbar[kUmStages];
+  __shared__ uint32_t tmem_slot;
+  const int m0 = blockIdx.y * kUmM, n0 = blockIdx.z * nt;
+  const long long kbeg = (long long)blockIdx.x * kchunk;
+  const long long kend = (kbeg + kchunk < ng) ? kbeg + kchunk : ng;
+  const int n_iter = (int)((kend - kbeg + kUmBK - 1) / kUmBK);
+  const size_t stage_bytes = umma_stage_bytes(nt);
+  int ncols = 32;
+  while (ncols < nt) ncols <<= 1;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kUmStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = make_idesc(kUmM, nt);
+  bool ok = true;
+  for (int it = 0; it < n_iter; ++it) {
+    const int s = it & 1;
+    bool w = true;
+    if (it >= kUmStages) w = mbar_wait(smem_u32(&mbar[s]), (uint32_t)((it / kUmStages - 1) & 1));
+    if (!__syncthreads_and(w)) {  // uniform decision: every thread leaves the loop together
+      ok = false;
+      break;
+    }
+    uint8_t *st = smem + s * stage_bytes;
+    produce_stage<AMODE>(st, nt, F, xi, M, m0, Y, Nn, n0, ng, kbeg + (long long)it * kUmBK, kend);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a_hi = smem_u32(st), a_lo = a_hi + kUmM * kUmBK * 2;
+      const uint32_t b_hi = a_lo + kUmM * kUmBK * 2, b_lo = b_hi + nt * kUmBK * 2;
+#pragma unroll
+      for (int t = 0; t < kUmBK / 16; ++t) {
+        const uint32_t o = t * 256;  // two core matrices (16 points) per MMA along K
+        const uint64_t dah = make_desc(a_hi + o, 128, 1024), dal = make_desc(a_lo + o, 128, 1024);
+        const uint64_t dbh = make_desc(b_hi + o, 128, 1024), dbl = make_desc(b_lo + o, 128, 1024);
+        mma_bf16(tmem, dah, dbh, idesc, (it > 0 || t > 0) ? 1u : 0u);
+        mma_bf16(tmem, dah, dbl, idesc, 1u);
+        mma_bf16(tmem, dal, dbh, idesc, 1u);
+      }
+      mma_commit(smem_u32(&mbar[s]));
+    }
+  }
+  // all committed MMAs done (commits complete in order: the last one covers the rest)
+  if (ok && n_iter > 0) {
+    const int last = n_iter - 1;
+    ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last / kUmStages) & 1)));
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    // give in-flight MMAs a further bounded chance to finish before the accumulator is freed
+    for (int s = 0; s < kUmStages; ++s) {
+      const int cnt = (n_iter - s + kUmStages - 1) / kUmStages;
+      if (cnt > 0) mbar_wait(smem_u32(&mbar[s]), (uint32_t)((cnt - 1) & 1));
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok && n_iter > 0) {
+    const int lane = threadIdx.x & 31;
+    const int m = m0 + warp * 32 + lane;
+    for (int c = 0; c < nt; c += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < M) {
+        double *o = part + ((long long)blockIdx.x * M + m) * Nn;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (n0 + c + j < Nn) o[n0 + c + j] = (double)__uint_as_float(r[j]);
+      }
+    }
+  } else if (n_iter == 0) {
+    const int lane = threadIdx.x & 31;
+    const int m = m0 + warp * 32 + lane;
+    if (m < M)
+      for (int c = 0; c < nt && n0 + c < Nn; ++c) part[((long long)blockIdx.x * M + m) * Nn + n0 + c] = 0.0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// tile width for Nn output columns: multiple of 16, at most 256
+static int umma_nt(int Nn) {
+  int nt = ((Nn + 15) / 16) * 16;
+  return nt > 256 ? 256 : nt;
+}
+
+static long long umma_kchunk(long long ng, int tiles) {
+  // about two CTAs per SM across all tiles, whole stages per chunk
+  long long target = 304 / (tiles > 0 ? tiles : 1);
+  if (target < 1) target = 1;
+  long long c = (ng + target - 1) / target;
+  c = ((c + kUmBK - 1) / kUmBK) * kUmBK;
+  return c < kUmBK ? kUmBK : c;
+}
+
+size_t umma_prod_gemm_work_bytes(int M, int Nn, long long ng) {
+  const int nt = umma_nt(Nn);
+  const int tiles = ((M + kUmM - 1) / kUmM) * ((Nn + nt - 1) / nt);
+  const long long kc = umma_kchunk(ng, tiles);
+  const long long chunks = (ng + kc - 1) / kc;
+  return (size_t)(chunks * M * Nn) * sizeof(double);
+}
+
+template <int AMODE>
+static int launch_umma(const float *F, const int2 *xi, int M, const float *Y, int Nn, long long ng,
+                       double scale, double *out, double *work, int *err, cudaStream_t s) {
+  const int nt = umma_nt(Nn);
+  const int tiles = ((M + kUmM - 1) / kUmM) * ((Nn + nt - 1) / nt);
+  const long long kc = umma_kchunk(ng, tiles);
+  const long long chunks = (ng + kc - 1) / kc;
+  const size_t smem = kUmStages * umma_stage_bytes(nt);
+  cudaFuncSetAttribute(k_umma_prod_gemm<AMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)chunks, (M + kUmM - 1) / kUmM, (Nn + nt - 1) / nt);
+  k_umma_prod_gemm<AMODE><<<grid, kUmThreads, smem, s>>>(F, xi, M, Y, Nn, nt, ng, kc, work, err);
+  count_launch(1);
+  launch_reduce_cols(work, (int)chunks, M * Nn, scale, out, s);
+  return 0;
+}
+
+int launch_umma_prod_gemm(const float *F, const int2 *xi, int M, const float *Y, int Nn, long long ng,
+                          double scale, double *out, double *work, int *err, cudaStream_t s) {
+  return launch_umma<UA_PRODUCT>(F, xi, M, Y, Nn, ng, scale, out, work, err, s);
+}
+
+// cleaning overlaps of Eq. (15): out[2c + h][s] = scale sum_r (Re, Im)_h d_c(r) phi_s(r)
+int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const float *phi, int n_occ,
+                              long long ng, double scale, double *out, double *work, int *err,
+                              cudaStream_t s) {
+  return launch_umma<UA_COMPLEX>(d_interleaved, nullptr, 2 * n_cols, phi, n_occ, ng, scale, out, work,
+                                 err, s);
+}
+
+}  // namespace sbse

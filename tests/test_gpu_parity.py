@@ -182,3 +182,29 @@ def test_mid48_full_launch_sampled_pair_fp64_and_mixed(B, mid48):
     assert rel_err(W32[k].reshape(48, 48, 48), w_ref) < 2e-3
     assert np.max(np.abs(A64 - A64.T)) < 1e-12
     assert np.max(np.abs(ev32 - ev64)) < 5 * MEV
+
+
+@pytest.mark.parametrize("name", ["tiny16", "mid48"])
+def test_tensor_core_exchange_contraction_matches_fp64(B, name, tiny16, mid48):
+    """(ia|jb) by the tcgen05 BF16-split GEMM (mixed mode) against the FP64 CUDA-core GEMM and the
+    oracle: the exchange matrix depends on the orbitals only, so the difference is the contraction
+    arithmetic alone (expected ~1e-6 relative for three-term BF16 splitting with FP32 sums)."""
+    s = tiny16 if name == "tiny16" else mid48
+    p = s.preset
+    K = {}
+    for prec, tc in ((B.SBSE_FP64, 1), (B.SBSE_MIXED, 1), (B.SBSE_MIXED, 0)):
+        with B.Context(0, prec) as c:
+            B.sbse_set_option(c.h, B.SBSE_OPT_TENSOR_CORES, tc)
+            c.set_grid(s.N, s.box, s.v_loc)
+            c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi[:p.n_occ + p.n_c], s.eps[:p.n_occ + p.n_c],
+                           p.scissor)
+            K[(prec, tc)] = c.build_A(B.SBSE_EXCHANGE)
+    diag = np.diag(np.diag(K[(B.SBSE_FP64, 1)]))
+    if name == "tiny16":
+        phi_o, _, phi_c, _ = tdh.windows(s.phi, s.eps, p.n_occ, p.n_o, p.n_c)
+        kref = tdh.exchange_K(tdh.Grid(s.N, s.box), phi_o, phi_c)
+        assert rel_err((K[(B.SBSE_FP64, 1)] - np.diag(np.diag(K[(B.SBSE_FP64, 1)]))) / 2,
+                       kref - np.diag(np.diag(kref))) < 1e-10
+    ref = K[(B.SBSE_FP64, 1)] - diag
+    assert rel_err(K[(B.SBSE_MIXED, 1)] - diag, ref) < 1e-4
+    assert rel_err(K[(B.SBSE_MIXED, 0)] - diag, ref) < 1e-4
