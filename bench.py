@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--n-steps", type=int, default=None, help="override the TDH step count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--chunk-mb", type=int, default=None, help="SBSE_OPT_CHUNK_MB (L2 chunking)")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -248,6 +249,8 @@ def main():
             torch.distributed.barrier()
 
     ctx = B.Context(local, prec)
+    if args.chunk_mb is not None:
+        B.sbse_set_option(ctx.h, B.SBSE_OPT_CHUNK_MB, args.chunk_mb)
     ctx.set_grid(pre.N, pre.box, system.v_loc)
     ctx.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi, eps, pre.scissor)
     ext = torch.cuda.ExternalStream(B.sbse_get_stream(ctx.h), device=dev)

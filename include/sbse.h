@@ -176,6 +176,11 @@ int sbse_get_stream(const sbse_ctx *ctx, void **stream);
  * sbse_build_A on the tensor cores (tcgen05, BF16 high/low split of both operands, three products
  * per term, FP32 accumulation); 0 uses FP32 CUDA-core arithmetic. Errors: INVALID_ARG. */
 #define SBSE_OPT_TENSOR_CORES 1
+/* SBSE_OPT_CHUNK_MB (default 0): sbse_apply_W advances the pairs in chunks holding about this many
+ * MiB of propagated orbitals, so that the three passes of a split-operator step find a chunk in the
+ * L2 cache; 0 advances all pairs at once (fastest as separate launches: small launches leave
+ * SMs idle). Results do not depend on it. */
+#define SBSE_OPT_CHUNK_MB 2
 int sbse_set_option(sbse_ctx *ctx, int option, int value);
 
 /* Number of CUDA kernel launches the library has issued in this process (all contexts), for

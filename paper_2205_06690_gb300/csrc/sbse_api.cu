@@ -72,6 +72,8 @@ struct sbse_ctx {
   int *flag = nullptr;
   // mixed mode: grid-sum contractions on the tensor cores (SBSE_OPT_TENSOR_CORES)
   int tensor_cores = 1;
+  // bytes of propagated orbitals per chunk of pairs (SBSE_OPT_CHUNK_MB); 0 = all pairs at once
+  double l2_chunk_bytes = 1e30;
   // profiling
   bool prof = false;
   PhaseClock clk;
@@ -465,6 +467,8 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     wts[n] = w * exp(-0.5 * p->gamma * p->gamma * t * t) * p->dt / p->alpha;
   }
   C *acur = a0, *anext = a1;
+  const double pair_bytes = (double)L * ng * sizeof(C);
+  const int chunk_pairs = std::max(1, std::min(P, (int)(ctx->l2_chunk_bytes / pair_bytes)));
   for (int n = 0; n < Nt; ++n) {
     bool pending = n > 0;
     if (M > 0 && n % M == 0) {
@@ -488,16 +492,22 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     xa.out = anext;
     xa.pv = pending ? g.pv_dt : g.pv_half;
     round_trip_orbitals<T>(ctx, g, xa, anext, L, nullptr, L, nullptr);
-    XfwdArgs<T> xb{};
-    xb.mode = XF_PHASE_PAIR;
-    xb.n_items = P * L;
-    xb.in = d;
-    xb.out = d;
-    xb.a = acur;
-    xb.em1 = em1;
-    xb.L = L;
-    xb.pv = pending ? g.pv_dt : g.pv_half;
-    round_trip_orbitals<T>(ctx, g, xb, d, P * L, anext, L, dn);
+    // the three passes run over chunks of pairs small enough to stay in L2 between the passes,
+    // so that each orbital crosses HBM about once per step instead of three times
+    for (int p0 = 0; p0 < P; p0 += chunk_pairs) {
+      const int pc = std::min(chunk_pairs, P - p0);
+      C *dc = d + (long long)p0 * L * ng;
+      XfwdArgs<T> xb{};
+      xb.mode = XF_PHASE_PAIR;
+      xb.n_items = pc * L;
+      xb.in = dc;
+      xb.out = dc;
+      xb.a = acur;
+      xb.em1 = em1 ? em1 + (long long)p0 * ng : nullptr;
+      xb.L = L;
+      xb.pv = pending ? g.pv_dt : g.pv_half;
+      round_trip_orbitals<T>(ctx, g, xb, dc, pc * L, anext, L, dn + (long long)p0 * ng);
+    }
     CHECK_LAUNCH("step");
     clk_end(ctx, c0);
     size_t c1 = 0;
@@ -886,6 +896,11 @@ int sbse_set_option(sbse_ctx *ctx, int option, int value) {
   if (!ctx) return SBSE_ERR_INVALID_ARG;
   if (option == SBSE_OPT_TENSOR_CORES) {
     ctx->tensor_cores = value != 0;
+    return SBSE_OK;
+  }
+  if (option == SBSE_OPT_CHUNK_MB) {
+    if (value < 0) return fail(ctx, SBSE_ERR_INVALID_ARG, "chunk size must be >= 0");
+    ctx->l2_chunk_bytes = value == 0 ? 1e30 : (double)value * (1 << 20);
     return SBSE_OK;
   }
   return fail(ctx, SBSE_ERR_INVALID_ARG, "unknown option");

@@ -208,3 +208,20 @@ def test_tensor_core_exchange_contraction_matches_fp64(B, name, tiny16, mid48):
     ref = K[(B.SBSE_FP64, 1)] - diag
     assert rel_err(K[(B.SBSE_MIXED, 1)] - diag, ref) < 1e-4
     assert rel_err(K[(B.SBSE_MIXED, 0)] - diag, ref) < 1e-4
+
+
+def test_pair_chunking_does_not_change_results(B, mid48):
+    """Advancing the pairs in L2-sized chunks (SBSE_OPT_CHUNK_MB) runs the same kernels on the same
+    items: the FP64 results are bitwise identical to advancing all pairs at once."""
+    s = mid48
+    p = s.preset
+    prm = B.TDHParams(n_s=10, n_steps=12, clean_every=5, dt=p.dt, gamma=p.gamma, alpha=p.alpha, seed=2)
+    out = []
+    for mb in (0, 20):
+        with B.Context(0, B.SBSE_FP64) as c:
+            B.sbse_set_option(c.h, B.SBSE_OPT_CHUNK_MB, mb)
+            c.set_grid(s.N, s.box, s.v_loc)
+            c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi[:p.n_occ + p.n_c], s.eps[:p.n_occ + p.n_c],
+                           p.scissor)
+            out.append(c.apply_W(prm, tdh.pair_list(p.n_o)[:7], copy_out=True))
+    assert np.array_equal(out[0], out[1])
