@@ -181,6 +181,11 @@ int sbse_get_stream(const sbse_ctx *ctx, void **stream);
  * L2 cache; 0 advances all pairs at once (fastest as separate launches: small launches leave
  * SMs idle). Results do not depend on it. */
 #define SBSE_OPT_CHUNK_MB 2
+/* SBSE_OPT_PERSISTENT (default 0): advance the eta0 set and all pairs by one split-operator step in
+ * a single persistent kernel whose blocks pull tiles from a dependency-ordered queue (grids with a
+ * register-pencil FFT); 0 uses three separate pass kernels, which are faster on GB300 (the merged
+ * kernel is register-limited to fewer resident warps). Results do not depend on it. */
+#define SBSE_OPT_PERSISTENT 3
 int sbse_set_option(sbse_ctx *ctx, int option, int value);
 
 /* Number of CUDA kernel launches the library has issued in this process (all contexts), for

@@ -45,6 +45,13 @@ int upload_reg_twiddles() {
   return 0;
 }
 
+// Loads of data that other blocks of the same launch may have written (persistent step kernel)
+// bypass L1, which is not coherent across SMs.
+template <bool COH, typename C> __device__ __forceinline__ C ldv(const C *p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
 // planes per block: the largest divisor of N with <= 256 threads and <= 96 KB of shared memory
 constexpr int plane_ppb(int N, int csize) {
   int best = 1;
@@ -60,17 +67,13 @@ template <typename T, int N> constexpr size_t plane_smem() {
 
 // ------------------------------------------------------------------------------------------
 
+// forward x and y FFTs of the PPB planes starting at plane offset `off` (= z0 N^2) of `item`, with
+// the fused pre-operation; S is the block's shared tile
 template <typename T, int N, bool PAIR>
-__global__ void __launch_bounds__(kPPB<T, N> * N)
-    k_plane_fwd(GView<T> g, XfwdArgs<T> a, long long planes_total) {
+__device__ __forceinline__ void fwd_planes(const GView<T> &g, const XfwdArgs<T> &a, long long item,
+                                           long long off, C2<T> *S) {
   using C = C2<T>;
   constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N, NT = PPB * N;
-  extern __shared__ unsigned char smem_raw[];
-  C *S = reinterpret_cast<C *>(smem_raw);
-  // PPB divides N: the block's planes z0 .. z0 + PPB - 1 are contiguous inside one item
-  const long long p0 = (long long)blockIdx.x * PPB;
-  const long long item = p0 / N;
-  const long long off = (p0 - item * N) * NN;
   const PreopItem<T> it = preop_item<T>(g, a, item);
   if constexpr (PAIR) {
     // the hot pre-operation of the pair batch: loads of 8 points are issued before any is used
@@ -129,18 +132,28 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(128) k_zcol(GView<T> g, C2<T> *data, long long cols_total, int mult) {
+template <typename T, int N, bool PAIR>
+__global__ void __launch_bounds__(kPPB<T, N> * N)
+    k_plane_fwd(GView<T> g, XfwdArgs<T> a, long long planes_total) {
+  constexpr int PPB = kPPB<T, N>, NN = N * N;
+  extern __shared__ unsigned char smem_raw[];
+  // PPB divides N: the block's planes z0 .. z0 + PPB - 1 are contiguous inside one item
+  const long long p0 = (long long)blockIdx.x * PPB;
+  const long long item = p0 / N;
+  fwd_planes<T, N, PAIR>(g, a, item, (p0 - item * N) * NN, reinterpret_cast<C2<T> *>(smem_raw));
+}
+
+// one (x, y) column of one item: forward z FFT, multiplier, inverse z FFT (thread per column)
+template <typename T, int N, bool COH>
+__device__ __forceinline__ void zcol_column(const GView<T> &g, C2<T> *data, long long item, int rem,
+                                            int mult) {
   using C = C2<T>;
   constexpr int NN = N * N;
-  const long long c = (long long)blockIdx.x * 128 + threadIdx.x;
-  if (c >= cols_total) return;
-  const long long item = c / NN;
-  const int rem = (int)(c - item * NN), y = rem / N, x = rem - y * N;
+  const int y = rem / N, x = rem - y * N;
   C *base = data + item * g.ng + rem;
   C v[N];
 #pragma unroll
-  for (int z = 0; z < N; ++z) v[z] = base[(long long)z * NN];
+  for (int z = 0; z < N; ++z) v[z] = ldv<COH>(base + (long long)z * NN);
   fft_reg<T, N, -1>(v);
   const T inv_ng = T(1) / T(N * N * N);
   if (mult == Z_KINETIC) {
@@ -160,6 +173,15 @@ __global__ void __launch_bounds__(128) k_zcol(GView<T> g, C2<T> *data, long long
   for (int z = 0; z < N; ++z) base[(long long)z * NN] = v[z];
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_zcol(GView<T> g, C2<T> *data, long long cols_total, int mult) {
+  constexpr int NN = N * N;
+  const long long c = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (c >= cols_total) return;
+  const long long item = c / NN;
+  zcol_column<T, N, false>(g, data, item, (int)(c - item * NN), mult);
+}
+
 enum PlaneInvMode { PI_PLAIN = 0, PI_DENSITY = 1, PI_POISSON = 2 };
 
 struct PlaneInvArgs {
@@ -169,7 +191,7 @@ struct PlaneInvArgs {
 };
 
 // y then x inverse transforms of PPB planes held in shared memory
-template <typename T, int N>
+template <typename T, int N, bool COH = false>
 __device__ __forceinline__ void plane_inverse(C2<T> *S, const C2<T> *src_item_plane0, int pl, int q) {
   using C = C2<T>;
   constexpr int LD = N + 1, NN = N * N;
@@ -177,7 +199,7 @@ __device__ __forceinline__ void plane_inverse(C2<T> *S, const C2<T> *src_item_pl
     C v[N];
     const C *col = src_item_plane0 + (long long)pl * NN + q;
 #pragma unroll
-    for (int y = 0; y < N; ++y) v[y] = col[y * N];
+    for (int y = 0; y < N; ++y) v[y] = ldv<COH>(col + y * N);
     fft_reg<T, N, +1>(v);
     C *dst = S + pl * N * LD + q;
 #pragma unroll
@@ -196,6 +218,55 @@ __device__ __forceinline__ void plane_inverse(C2<T> *S, const C2<T> *src_item_pl
   __syncthreads();
 }
 
+// y, x inverse FFTs of the planes z0 .. z0 + PPB - 1 of the L orbitals of `pair`, storing each and
+// accumulating the induced density 2 sum_l (2 Re(conj(eta0_l) d_l) + |d_l|^2) (Eq. 11)
+template <typename T, int N, bool COH>
+__device__ __forceinline__ void inv_density_planes(const GView<T> &g, C2<T> *data, const C2<T> *a_next,
+                                                   T *dens, int pair, int L, int z0, C2<T> *S) {
+  using C = C2<T>;
+  constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N, NT = PPB * N;
+  const int pl = threadIdx.x / N, q = threadIdx.x - pl * N;
+  T accd[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) accd[k] = T(0);
+  for (int ell = 0; ell < L; ++ell) {
+    const long long item = (long long)pair * L + ell;
+    C *base = data + item * g.ng + (long long)z0 * NN;
+    plane_inverse<T, N, COH>(S, base, pl, q);
+    const C *ab = a_next + (long long)ell * g.ng + (long long)z0 * NN;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int l = threadIdx.x + k * NT;
+      const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
+      const C dv = S[(p * N + y) * LD + x];
+      base[l] = dv;
+      const C a0 = ldv<COH>(ab + l);
+      accd[k] += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+    }
+    __syncthreads();
+  }
+  T *db = dens + (long long)pair * g.ng + (long long)z0 * NN;
+#pragma unroll
+  for (int k = 0; k < N; ++k) db[threadIdx.x + k * NT] = accd[k];
+}
+
+// y, x inverse FFTs of the PPB planes at plane offset `off` of `item`, stored back in place
+template <typename T, int N, bool COH>
+__device__ __forceinline__ void inv_plain_planes(const GView<T> &g, C2<T> *data, long long item,
+                                                 long long off, C2<T> *S) {
+  using C = C2<T>;
+  constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N, NT = PPB * N;
+  const int pl = threadIdx.x / N, q = threadIdx.x - pl * N;
+  C *base = data + item * g.ng + off;
+  plane_inverse<T, N, COH>(S, base, pl, q);
+#pragma unroll 4
+  for (int k = 0; k < N; ++k) {
+    const int l = threadIdx.x + k * NT;
+    const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
+    base[l] = S[(p * N + y) * LD + x];
+  }
+}
+
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(kPPB<T, N> * N)
     k_plane_inv(GView<T> g, C2<T> *data, const C2<T> *a_next, T *dens, T *u_out, T *acc,
@@ -207,35 +278,16 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
   const int pl = threadIdx.x / N, q = threadIdx.x - pl * N;
   if (MODE == PI_DENSITY) {
     // blockIdx.y = pair, blockIdx.x = group of PPB planes of each of its L orbitals
-    const int pair = blockIdx.y;
-    const int z0 = blockIdx.x * PPB;
-    T accd[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) accd[k] = T(0);
-    for (int ell = 0; ell < pa.L; ++ell) {
-      const long long item = (long long)pair * pa.L + ell;
-      C *base = data + item * g.ng + (long long)z0 * NN;
-      plane_inverse<T, N>(S, base, pl, q);
-      const C *ab = a_next + (long long)ell * g.ng + (long long)z0 * NN;
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const int l = threadIdx.x + k * NT;
-        const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
-        const C dv = S[(p * N + y) * LD + x];
-        base[l] = dv;
-        const C a0 = ab[l];
-        accd[k] += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
-      }
-      __syncthreads();
-    }
-    T *db = dens + (long long)pair * g.ng + (long long)z0 * NN;
-#pragma unroll
-    for (int k = 0; k < N; ++k) db[threadIdx.x + k * NT] = accd[k];
+    inv_density_planes<T, N, false>(g, data, a_next, dens, blockIdx.y, pa.L, blockIdx.x * PPB, S);
     return;
   }
   const long long p0 = (long long)blockIdx.x * PPB;  // PPB divides N: all planes of one item
   const long long item = p0 / N;
   const long long off = (p0 - item * N) * NN;
+  if (MODE == PI_PLAIN) {
+    inv_plain_planes<T, N, false>(g, data, item, off, S);
+    return;
+  }
   C *base = data + item * g.ng + off;
   plane_inverse<T, N>(S, base, pl, q);
 #pragma unroll 4
@@ -243,9 +295,7 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
     const int l = threadIdx.x + k * NT;
     const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
     const C v = S[(p * N + y) * LD + x];
-    if (MODE == PI_PLAIN) {
-      base[l] = v;
-    } else {
+    {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const long long kk = 2 * item + h;
@@ -261,10 +311,93 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
 }
 
 // ------------------------------------------------------------------------------------------
+// Persistent split-operator step: one launch advances the eta0 set and every pair's L orbitals by
+// one step of Eq. (10) and writes each pair's induced density. Blocks claim tiles from a host-built
+// queue; a tile waits (bounded) for the tiles it reads, whose queue positions are always earlier,
+// so every awaited tile is held by a running block and the launch cannot deadlock. The queue
+// pipelines pairs (forward tiles of pair j, z tiles of pair j-1, inverse tiles of pair j-2) so that
+// the orbitals in flight stay in L2 between the three passes.
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// bounded wait for *p >= target (about a second at most); false on timeout
+__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target) {
+  for (unsigned i = 0; i < (1u << 23); ++i) {
+    if (ld_acquire(p) >= target) return true;
+    __nanosleep(100);
+  }
+  return false;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kPPB<T, N> * N)
+    k_step_persistent(GView<T> g, XfwdArgs<T> fa, XfwdArgs<T> fp, C2<T> *a_next, C2<T> *d, T *dens,
+                      int L, StepQueue q) {
+  using C = C2<T>;
+  constexpr int PPB = kPPB<T, N>, NN = N * N, G = N / PPB, NT = PPB * N;
+  extern __shared__ unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  __shared__ int4 cur;
+  __shared__ int go;
+  const unsigned tgt = (q.epoch + 1) * (unsigned)G;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned i = atomicAdd(q.claim, 1u) - q.claim_base;
+      const int4 it = (i < (unsigned)q.n_items) ? q.items[i] : make_int4(-1, 0, 0, 0);
+      bool ok = true;
+      if (it.x == SI_A_Z) {
+        ok = wait_geq(q.a_fwd + it.y, tgt);
+      } else if (it.x == SI_A_INV) {
+        ok = wait_geq(q.a_z + it.y, tgt);
+      } else if (it.x == SI_P_Z) {
+        ok = wait_geq(q.p_fwd + it.y, tgt);
+      } else if (it.x == SI_P_INV) {
+        ok = wait_geq(q.a_inv, (q.epoch + 1) * (unsigned)(L * G));
+        for (int l = 0; l < L && ok; ++l) ok = wait_geq(q.p_z + it.y * L + l, tgt);
+      }
+      if (!ok) atomicExch(q.err, 1);
+      __threadfence();
+      cur = it;
+      go = ok ? 1 : 0;
+    }
+    __syncthreads();
+    const int4 it = cur;
+    if (it.x < 0) break;
+    if (go) {
+      switch (it.x) {
+        case SI_A_FWD: fwd_planes<T, N, false>(g, fa, it.y, (long long)it.z * PPB * NN, S); break;
+        case SI_P_FWD: fwd_planes<T, N, true>(g, fp, it.y, (long long)it.z * PPB * NN, S); break;
+        case SI_A_Z: zcol_column<T, N, true>(g, a_next, it.y, it.z * NT + threadIdx.x, Z_KINETIC); break;
+        case SI_P_Z: zcol_column<T, N, true>(g, d, it.y, it.z * NT + threadIdx.x, Z_KINETIC); break;
+        case SI_A_INV: inv_plain_planes<T, N, true>(g, a_next, it.y, (long long)it.z * PPB * NN, S); break;
+        case SI_P_INV: inv_density_planes<T, N, true>(g, d, a_next, dens, it.y, L, it.z * PPB, S); break;
+        default: break;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      unsigned *c = nullptr;
+      if (it.x == SI_A_FWD) c = q.a_fwd + it.y;
+      else if (it.x == SI_A_Z) c = q.a_z + it.y;
+      else if (it.x == SI_A_INV) c = q.a_inv;
+      else if (it.x == SI_P_FWD) c = q.p_fwd + it.y;
+      else if (it.x == SI_P_Z) c = q.p_z + it.y;
+      if (c) atomicAdd(c, 1u);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // dispatch over the compile-time sizes
 
 template <typename T, int N> static void set_attrs() {
   const int sm = (int)plane_smem<T, N>();
+  cudaFuncSetAttribute(k_step_persistent<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_fwd<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_fwd<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -273,6 +406,26 @@ template <typename T, int N> static void set_attrs() {
 }
 
 template <typename T> struct FastOps {
+  template <int N>
+  static void step(const GridTables<T> &g, const XfwdArgs<T> &fa, const XfwdArgs<T> &fp, C2<T> *a_next,
+                   C2<T> *d, T *dens, int L, const StepQueue &q, int grid, cudaStream_t s) {
+    if constexpr (!(sizeof(T) == 8 && N > 48)) {
+      k_step_persistent<T, N><<<grid, kPPB<T, N> * N, plane_smem<T, N>(), s>>>(view(g), fa, fp, a_next, d,
+                                                                              dens, L, q);
+    }
+  }
+  template <int N> static int resident_blocks() {
+    if constexpr (!(sizeof(T) == 8 && N > 48)) {
+      int per_sm = 0, dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent<T, N>, kPPB<T, N> * N,
+                                                    plane_smem<T, N>());
+      return per_sm * sms;
+    }
+    return 0;
+  }
+  template <int N> static int tiles_per_orbital() { return N / kPPB<T, N>; }
   template <int N> static void fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s) {
     if constexpr (!(sizeof(T) == 8 && N > 48)) {
       const long long planes = (long long)a.n_items * N;
@@ -326,6 +479,32 @@ template <typename T> struct FastOps {
     default: break;                    \
   }
 
+template <typename T>
+void launch_step_persistent(const GridTables<T> &g, const XfwdArgs<T> &fa, const XfwdArgs<T> &fp,
+                            C2<T> *a_next, C2<T> *d, T *dens, int L, const StepQueue &q, int grid,
+                            cudaStream_t s) {
+#define SBSE_CALL(n) FastOps<T>::template step<n>(g, fa, fp, a_next, d, dens, L, q, grid, s)
+  SBSE_FAST_SWITCH(g.N, SBSE_CALL)
+#undef SBSE_CALL
+  count_launch(1);
+}
+
+template <typename T> int step_resident_blocks(int N) {
+  int r = 0;
+#define SBSE_CALL(n) r = FastOps<T>::template resident_blocks<n>()
+  SBSE_FAST_SWITCH(N, SBSE_CALL)
+#undef SBSE_CALL
+  return r;
+}
+
+template <typename T> int step_tiles_per_orbital(int N) {
+  int r = 0;
+#define SBSE_CALL(n) r = FastOps<T>::template tiles_per_orbital<n>()
+  SBSE_FAST_SWITCH(N, SBSE_CALL)
+#undef SBSE_CALL
+  return r;
+}
+
 template <typename T> bool fast_supported(int N) {
   // FP64 pencils of 64 would not fit in the register file
   for (int i = 0; i < kRegCount; ++i)
@@ -376,6 +555,11 @@ void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, con
 }
 
 #define SBSE_FAST_INST(T)                                                                           \
+  template void launch_step_persistent<T>(const GridTables<T> &, const XfwdArgs<T> &,              \
+                                          const XfwdArgs<T> &, C2<T> *, C2<T> *, T *, int,         \
+                                          const StepQueue &, int, cudaStream_t);                   \
+  template int step_resident_blocks<T>(int);                                                       \
+  template int step_tiles_per_orbital<T>(int);                                                     \
   template bool fast_supported<T>(int);                                                            \
   template void init_fast_kernels<T>();                                                            \
   template void launch_plane_fwd<T>(const GridTables<T> &, const XfwdArgs<T> &, cudaStream_t);     \

@@ -86,6 +86,26 @@ template <typename T> void launch_xinv_poisson(const GridTables<T> &g, C2<T> *da
 // acc64 += acc, acc = 0
 template <typename T> void launch_flush_acc(double *acc64, T *acc, long long n, cudaStream_t s);
 
+// ---- persistent split-operator step (fft_fast.cu): tile queue and completion counters
+enum StepItemKind { SI_A_FWD = 0, SI_A_Z = 1, SI_A_INV = 2, SI_P_FWD = 3, SI_P_Z = 4, SI_P_INV = 5 };
+struct StepQueue {
+  const int4 *items;    // {kind, orbital (or pair for SI_P_INV), tile, 0}, dependency-ordered
+  int n_items;
+  unsigned *claim;      // claim counter, monotonic over the launches of one sbse_apply_W
+  unsigned claim_base;  // its value when this launch starts
+  unsigned *a_fwd, *a_z;  // per eta0 orbital
+  unsigned *a_inv;        // all eta0 inverse tiles
+  unsigned *p_fwd, *p_z;  // per pair orbital
+  unsigned epoch;         // launch index: completion targets are (epoch + 1) x tiles
+  int *err;               // set when a bounded wait times out
+};
+template <typename T>
+void launch_step_persistent(const GridTables<T> &g, const XfwdArgs<T> &fa, const XfwdArgs<T> &fp,
+                            C2<T> *a_next, C2<T> *d, T *dens, int L, const StepQueue &q, int grid,
+                            cudaStream_t s);
+template <typename T> int step_resident_blocks(int N);
+template <typename T> int step_tiles_per_orbital(int N);
+
 // ---- elementwise and reduction kernels (tdh_kernels.cu)
 template <typename T> void launch_init_a(const GridTables<T> &g, const double *phi, int n_occ,
                                          const double *coeff, int L, C2<T> *a, double *part,

@@ -72,6 +72,8 @@ struct sbse_ctx {
   int *flag = nullptr;
   // mixed mode: grid-sum contractions on the tensor cores (SBSE_OPT_TENSOR_CORES)
   int tensor_cores = 1;
+  // split-operator step as one persistent kernel (SBSE_OPT_PERSISTENT)
+  int persistent = 0;
   // bytes of propagated orbitals per chunk of pairs (SBSE_OPT_CHUNK_MB); 0 = all pairs at once
   double l2_chunk_bytes = 1e30;
   // profiling
@@ -83,7 +85,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -467,6 +469,49 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     wts[n] = w * exp(-0.5 * p->gamma * p->gamma * t * t) * p->dt / p->alpha;
   }
   C *acur = a0, *anext = a1;
+  // persistent step kernel: dependency-ordered tile queue and completion counters
+  const bool persistent = ctx->persistent && fast_supported<T>(ctx->N);
+  StepQueue sq{};
+  int step_grid = 0;
+  long long epoch = 0;
+  if (persistent) {
+    const int G = step_tiles_per_orbital<T>(ctx->N);
+    std::vector<int4> items;
+    auto add_orb = [&](int kind, int o) {
+      for (int t = 0; t < G; ++t) items.push_back(make_int4(kind, o, t, 0));
+    };
+    auto fwd_pair = [&](int j) { for (int l = 0; l < L; ++l) add_orb(SI_P_FWD, j * L + l); };
+    auto z_pair = [&](int j) { for (int l = 0; l < L; ++l) add_orb(SI_P_Z, j * L + l); };
+    auto inv_pair = [&](int j) { for (int t = 0; t < G; ++t) items.push_back(make_int4(SI_P_INV, j, t, 0)); };
+    for (int l = 0; l < L; ++l) add_orb(SI_A_FWD, l);
+    fwd_pair(0);
+    for (int l = 0; l < L; ++l) add_orb(SI_A_Z, l);
+    if (P > 1) fwd_pair(1);
+    z_pair(0);
+    for (int l = 0; l < L; ++l) add_orb(SI_A_INV, l);
+    for (int j = 2; j < P + 2; ++j) {  // pair j forward, pair j-1 z, pair j-2 inverse + density
+      if (j < P) fwd_pair(j);
+      if (j - 1 < P) z_pair(j - 1);
+      inv_pair(j - 2);
+    }
+    const size_t n_cnt = 2 + 2 * (size_t)L + 2 * (size_t)P * L;
+    if ((rc = ensure(ctx, WS_QUEUE, items.size() * sizeof(int4) + n_cnt * sizeof(unsigned), &vp))) return rc;
+    int4 *items_dev = (int4 *)vp;
+    unsigned *cnt = (unsigned *)(items_dev + items.size());
+    CK(cudaMemcpyAsync(items_dev, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(cnt, 0, n_cnt * sizeof(unsigned), st));
+    sq.items = items_dev;
+    sq.n_items = (int)items.size();
+    sq.claim = cnt;
+    sq.a_fwd = cnt + 1;
+    sq.a_z = sq.a_fwd + L;
+    sq.a_inv = sq.a_z + L;
+    sq.p_fwd = sq.a_inv + 1;
+    sq.p_z = sq.p_fwd + (size_t)P * L;
+    sq.err = ctx->flag;
+    step_grid = step_resident_blocks<T>(ctx->N);
+    if (step_grid <= 0) return fail(ctx, SBSE_ERR_CUDA, "persistent step kernel cannot be resident");
+  }
   const double pair_bytes = (double)L * ng * sizeof(C);
   const int chunk_pairs = std::max(1, std::min(P, (int)(ctx->l2_chunk_bytes / pair_bytes)));
   for (int n = 0; n < Nt; ++n) {
@@ -491,6 +536,24 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     xa.in = acur;
     xa.out = anext;
     xa.pv = pending ? g.pv_dt : g.pv_half;
+    if (persistent) {
+      XfwdArgs<T> xb{};
+      xb.mode = XF_PHASE_PAIR;
+      xb.n_items = P * L;
+      xb.in = d;
+      xb.out = d;
+      xb.a = acur;
+      xb.em1 = em1;
+      xb.L = L;
+      xb.pv = xa.pv;
+      sq.claim_base = (unsigned)(epoch * (unsigned long long)(sq.n_items + step_grid));
+      sq.epoch = (unsigned)epoch;
+      launch_step_persistent<T>(g, xa, xb, anext, d, dn, L, sq, step_grid, st);
+      ++epoch;
+      CHECK_LAUNCH("persistent step");
+      clk_end(ctx, c0);
+      goto poisson_step;
+    }
     round_trip_orbitals<T>(ctx, g, xa, anext, L, nullptr, L, nullptr);
     // the three passes run over chunks of pairs small enough to stay in L2 between the passes,
     // so that each orbital crosses HBM about once per step instead of three times
@@ -510,6 +573,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     }
     CHECK_LAUNCH("step");
     clk_end(ctx, c0);
+  poisson_step:
     size_t c1 = 0;
     clk_begin(ctx, 1, &c1);
     const bool recomputed = (M > 0 && (n + 1) % M == 0 && n + 1 < Nt);
@@ -525,7 +589,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     int h = 0;
     CK(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (h) return fail(ctx, SBSE_ERR_DEVICE_TIMEOUT, "cleaning overlaps: wait on the tensor cores timed out");
+    if (h) return fail(ctx, SBSE_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out (persistent step or tensor-core cleaning)");
   }
   // results into the canonical slots
   for (int k = 0; k < P; ++k)
@@ -896,6 +960,10 @@ int sbse_set_option(sbse_ctx *ctx, int option, int value) {
   if (!ctx) return SBSE_ERR_INVALID_ARG;
   if (option == SBSE_OPT_TENSOR_CORES) {
     ctx->tensor_cores = value != 0;
+    return SBSE_OK;
+  }
+  if (option == SBSE_OPT_PERSISTENT) {
+    ctx->persistent = value != 0;
     return SBSE_OK;
   }
   if (option == SBSE_OPT_CHUNK_MB) {

@@ -225,3 +225,22 @@ def test_pair_chunking_does_not_change_results(B, mid48):
                            p.scissor)
             out.append(c.apply_W(prm, tdh.pair_list(p.n_o)[:7], copy_out=True))
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_persistent_step_matches_pass_kernels(B, mid48, prec):
+    """The persistent step kernel runs the same tile arithmetic as the three pass kernels, only
+    scheduled from a queue: results are bitwise identical (7 pairs, odd count; cleaning every 5)."""
+    s = mid48
+    p = s.preset
+    prm = B.TDHParams(n_s=10, n_steps=12, clean_every=5, dt=p.dt, gamma=p.gamma, alpha=p.alpha, seed=4)
+    precision = B.SBSE_FP64 if prec == "fp64" else B.SBSE_MIXED
+    out = []
+    for persistent in (0, 1):
+        with B.Context(0, precision) as c:
+            B.sbse_set_option(c.h, B.SBSE_OPT_PERSISTENT, persistent)
+            c.set_grid(s.N, s.box, s.v_loc)
+            c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi[:p.n_occ + p.n_c], s.eps[:p.n_occ + p.n_c],
+                           p.scissor)
+            out.append(c.apply_W(prm, tdh.pair_list(p.n_o)[3:10], copy_out=True))
+    assert np.array_equal(out[0], out[1])
