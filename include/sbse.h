@@ -129,6 +129,16 @@ int sbse_coefficients(uint64_t seed, int n_s, int n_occ, int dist, double *out);
 int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int *pi,
                  const int *pj, const double *coeff, double *w_out);
 
+/* Store externally computed screened potentials W_ij (for example from the learned surrogate) for
+ * n_pairs pairs (pi[k] <= pj[k] < n_o), so that sbse_build_A uses them instead of running
+ * sbse_apply_W for these pairs. w: host, n_pairs x n^3 doubles, copied.
+ * Requires sbse_set_orbitals. Errors: INVALID_ARG, NOT_READY, NUMERIC, CUDA. */
+int sbse_set_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, const double *w);
+
+/* Copy W_ij of n_pairs pairs out of the context (host, n_pairs x n^3 doubles). Errors: INVALID_ARG,
+ * NOT_READY (a pair has no W yet), CUDA. */
+int sbse_get_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, double *w);
+
 /* Assemble the Tamm-Dancoff matrix of Eq. (1), in FP64:
  *   A(ia, jb) = (eps_a - eps_i + Delta) delta_ij delta_ab + 2 (ia|jb) - (phi_a phi_b|W|phi_i phi_j)
  * with (ia|jb) = sum_r phi_i phi_a (r) [v phi_j phi_b](r) h^3 (exchange element after Eq. 1) and
@@ -200,6 +210,41 @@ int sbse_kernel_launches(long long *count);
  *        4 = A assembly + eigensolve. Errors: INVALID_ARG, CUDA. */
 int sbse_profile(sbse_ctx *ctx, int enable);
 int sbse_phase_time(sbse_ctx *ctx, int phase, double *ms, long long *launches);
+
+/* ---- learned surrogate (not in the paper; the workload's learned form) ----------------------
+ * A Fourier neural operator mapping (rho_ij, V_loc) on an n^3 grid to W^pol_ij: lift 2 -> width
+ * channels, `layers` Fourier layers U = K(V) + W V + b with K(V) = irfftn(R . rfftn(V)) on the kept
+ * modes kx < modes, ky, kz in [0, modes) U [n - modes, n), V' = GELU(U) except after the last layer,
+ * then a linear projection to one channel. Spectral and pointwise weights are used in BF16, sums in
+ * FP32; FP32 master weights and Adam moments are kept on the device.
+ * Parameter vector (FP32, sbse_fno_num_params entries): lift W [width][2], lift b [width], then per
+ * layer spectral R [2 modes][2 modes][modes][width][width] complex (re, im interleaved), pointwise
+ * W [width][width] (W[co][ci]), b [width]; then projection w [width], b [1].
+ * Tensors are DEVICE pointers, FP32: x [batch][2][n^3] (channel 0 = rho, 1 = V_loc), y and targets
+ * [batch][n^3]. Calls are synchronous. Errors: INVALID_ARG, OOM, CUDA. */
+typedef struct sbse_fno sbse_fno;
+int sbse_fno_create(sbse_fno **out, int device, int n, int width, int modes, int layers, int max_batch);
+void sbse_fno_destroy(sbse_fno *fno);
+const char *sbse_fno_last_error(const sbse_fno *fno);
+long long sbse_fno_num_params(const sbse_fno *fno);
+/* copy the FP32 parameter vector in (resets the Adam state) / out (params and/or last gradients) */
+int sbse_fno_set_params(sbse_fno *fno, const float *host);
+int sbse_fno_get_params(sbse_fno *fno, float *host, float *grad_host);
+int sbse_fno_forward(sbse_fno *fno, int batch, const float *x_dev, float *y_dev);
+/* forward, then backward from dL/dy = dy_dev: gradients available through sbse_fno_get_params */
+int sbse_fno_gradients(sbse_fno *fno, int batch, const float *x_dev, const float *dy_dev);
+/* one Adam step (b1 0.9, b2 0.999, eps 1e-8) on the loss 0.5 mean((y - t)^2); *loss receives it */
+int sbse_fno_train_step(sbse_fno *fno, int batch, const float *x_dev, const float *t_dev, float lr,
+                        double *loss);
+/* Surrogate inputs of pairs (i, j) of ctx's valence window, written to x_dev [n_pairs][2][n^3]:
+ * channel 0 = phi_i phi_j / s_rho, channel 1 = V_loc / s_v. Errors: INVALID_ARG, NOT_READY, CUDA. */
+int sbse_fno_pair_inputs(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, double s_rho, double s_v,
+                         float *x_dev);
+/* Surrogate screened potentials: W_ij = s_w * FNO(phi_i phi_j / s_rho, V_loc / s_v) for n_pairs pairs,
+ * stored in ctx as if computed by sbse_apply_W (the grid of fno must equal ctx's). Errors:
+ * INVALID_ARG, NOT_READY, SHAPE, OOM, CUDA. */
+int sbse_surrogate_W(sbse_ctx *ctx, sbse_fno *fno, int n_pairs, const int *pi, const int *pj, double s_rho,
+                     double s_v, double s_w);
 
 #ifdef __cplusplus
 }

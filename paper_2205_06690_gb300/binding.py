@@ -88,6 +88,8 @@ def load() -> C.CDLL:
         "sbse_coefficients": (i, [C.c_uint64, i, i, i, dp]),
         "sbse_apply_W": (i, [vp, C.POINTER(sbse_tdh_params), i, ip, ip, dp, dp]),
         "sbse_build_A": (i, [vp, C.c_uint, dp]),
+        "sbse_set_W": (i, [vp, i, ip, ip, dp]),
+        "sbse_get_W": (i, [vp, i, ip, ip, dp]),
         "sbse_spectrum": (i, [vp, i, dp, dp]),
         "sbse_last_error": (C.c_char_p, [vp]),
         "sbse_get_stream": (i, [vp, C.POINTER(vp)]),
@@ -97,6 +99,20 @@ def load() -> C.CDLL:
         "sbse_spectrum_noalloc": (i, [vp, i, i, vp, vp]),
         "sbse_phase_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
     }
+    fp = C.POINTER(C.c_float)
+    sig.update({
+        "sbse_fno_create": (i, [C.POINTER(vp), i, i, i, i, i, i]),
+        "sbse_fno_destroy": (None, [vp]),
+        "sbse_fno_last_error": (C.c_char_p, [vp]),
+        "sbse_fno_num_params": (C.c_longlong, [vp]),
+        "sbse_fno_set_params": (i, [vp, fp]),
+        "sbse_fno_get_params": (i, [vp, fp, fp]),
+        "sbse_fno_forward": (i, [vp, i, vp, vp]),
+        "sbse_fno_gradients": (i, [vp, i, vp, vp]),
+        "sbse_fno_train_step": (i, [vp, i, vp, vp, C.c_float, dp]),
+        "sbse_fno_pair_inputs": (i, [vp, i, ip, ip, d, d, vp]),
+        "sbse_surrogate_W": (i, [vp, vp, i, ip, ip, d, d, d]),
+    })
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
         f.restype = res
@@ -176,6 +192,40 @@ def sbse_apply_W(ctx, params: TDHParams, pairs, coeff=None, n_g: int | None = No
     return out
 
 
+def sbse_set_W(ctx, pairs, w) -> None:
+    """Store W_ij (n_pairs x n^3, host) for `pairs` [(i, j), ...]."""
+    pi = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
+    pj = np.ascontiguousarray([p[1] for p in pairs], dtype=np.int32)
+    wa = _f64(w)
+    ip = C.POINTER(C.c_int)
+    _check(ctx, load().sbse_set_W(ctx, len(pairs), pi.ctypes.data_as(ip), pj.ctypes.data_as(ip),
+                                  _dptr(wa)))
+
+
+def _pairs_c(pairs):
+    pi = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
+    pj = np.ascontiguousarray([p[1] for p in pairs], dtype=np.int32)
+    ip = C.POINTER(C.c_int)
+    return pi, pj, pi.ctypes.data_as(ip), pj.ctypes.data_as(ip)
+
+
+def sbse_get_W(ctx, pairs, n_g: int):
+    pi, pj, a, b = _pairs_c(pairs)
+    out = np.empty((len(pairs), n_g))
+    _check(ctx, load().sbse_get_W(ctx, len(pairs), a, b, _dptr(out)))
+    return out
+
+
+def sbse_fno_pair_inputs(ctx, pairs, s_rho: float, s_v: float, x_ptr: int) -> None:
+    pi, pj, a, b = _pairs_c(pairs)
+    _check(ctx, load().sbse_fno_pair_inputs(ctx, len(pairs), a, b, s_rho, s_v, C.c_void_p(x_ptr)))
+
+
+def sbse_surrogate_W(ctx, fno_handle, pairs, s_rho: float, s_v: float, s_w: float) -> None:
+    pi, pj, a, b = _pairs_c(pairs)
+    _check(ctx, load().sbse_surrogate_W(ctx, fno_handle, len(pairs), a, b, s_rho, s_v, s_w))
+
+
 def sbse_build_A(ctx, terms: int = SBSE_EXCHANGE | SBSE_DIRECT, n: int | None = None):
     """Assemble A on the device; returns it (n x n) when n = n_o * n_c is given."""
     out = None if n is None else np.empty((n, n))
@@ -220,6 +270,59 @@ def sbse_phase_time(ctx, phase: int):
     n = C.c_longlong()
     _check(ctx, load().sbse_phase_time(ctx, phase, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def _fcheck(h, rc):
+    if rc != SBSE_OK:
+        msg = load().sbse_fno_last_error(h) if h else None
+        raise SbseError(rc, (msg.decode() if msg else "") or sbse_last_error(None))
+
+
+class FNO:
+    """Owning wrapper of the FNO surrogate (sbse_fno_*). Tensor arguments are device pointers
+    (ints, e.g. torch's data_ptr()) of FP32 arrays."""
+
+    def __init__(self, n, width=32, modes=12, layers=4, max_batch=4, device=0):
+        h = C.c_void_p()
+        _fcheck(None, load().sbse_fno_create(C.byref(h), device, n, width, modes, layers, max_batch))
+        self.h = h
+        self.n, self.width, self.modes, self.layers = n, width, modes, layers
+        self.n_params = int(load().sbse_fno_num_params(h))
+
+    def close(self):
+        if self.h:
+            load().sbse_fno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        assert a.size == self.n_params
+        _fcheck(self.h, load().sbse_fno_set_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def get_params(self):
+        p = np.empty(self.n_params, np.float32)
+        g = np.empty(self.n_params, np.float32)
+        fp = C.POINTER(C.c_float)
+        _fcheck(self.h, load().sbse_fno_get_params(self.h, p.ctypes.data_as(fp), g.ctypes.data_as(fp)))
+        return p, g
+
+    def forward(self, batch, x_ptr, y_ptr):
+        _fcheck(self.h, load().sbse_fno_forward(self.h, batch, C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+    def gradients(self, batch, x_ptr, dy_ptr):
+        _fcheck(self.h, load().sbse_fno_gradients(self.h, batch, C.c_void_p(x_ptr), C.c_void_p(dy_ptr)))
+
+    def train_step(self, batch, x_ptr, t_ptr, lr):
+        loss = C.c_double()
+        _fcheck(self.h, load().sbse_fno_train_step(self.h, batch, C.c_void_p(x_ptr), C.c_void_p(t_ptr),
+                                                   C.c_float(lr), C.byref(loss)))
+        return loss.value
 
 
 class Context:

@@ -706,6 +706,30 @@ template <typename T> int run_build_A(sbse_ctx *ctx, unsigned terms) {
 
 }  // namespace
 
+// ---- accessors for the surrogate entry points (fno.cu)
+namespace sbse {
+struct CtxView {
+  int N, n_occ, n_o, device;
+  long long ng;
+  const float *phi32;
+  const double *v64;
+  double *W;
+  cudaStream_t stream;
+};
+int ctx_view(sbse_ctx *ctx, CtxView *v) {
+  if (!ctx || ctx->n_states == 0) return SBSE_ERR_NOT_READY;
+  *v = CtxView{ctx->N, ctx->n_occ, ctx->n_o, ctx->device, ctx->ng, ctx->phi32, ctx->v64, ctx->W, ctx->stream};
+  return SBSE_OK;
+}
+int ctx_pair_slot(sbse_ctx *ctx, int i, int j) { return pair_index(ctx->n_o, i, j); }
+void ctx_mark_pair(sbse_ctx *ctx, int slot) {
+  ctx->have[slot] = 1;
+  ctx->have_A = false;
+}
+void ctx_set_error(sbse_ctx *ctx, const std::string &m) { ctx->err = m; }
+}  // namespace sbse
+
+
 // =============================================================================================
 extern "C" {
 
@@ -914,6 +938,48 @@ int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int
     for (int k = 0; k < n_pairs; ++k)
       CK(cudaMemcpy(w_out + (long long)k * ctx->ng, ctx->W + (long long)slots[k] * ctx->ng,
                     ctx->ng * sizeof(double), cudaMemcpyDeviceToHost));
+  return SBSE_OK;
+}
+
+int sbse_get_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, double *w) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (!pi || !pj || !w || n_pairs < 1) return fail(ctx, SBSE_ERR_INVALID_ARG, "pairs or w missing");
+  CK(cudaSetDevice(ctx->device));
+  for (int k = 0; k < n_pairs; ++k) {
+    if (pi[k] < 0 || pj[k] < pi[k] || pj[k] >= ctx->n_o)
+      return fail(ctx, SBSE_ERR_INVALID_ARG, "pair indices must satisfy 0 <= i <= j < n_o");
+    const int slot = pair_index(ctx->n_o, pi[k], pj[k]);
+    if (!ctx->have[slot]) return fail(ctx, SBSE_ERR_NOT_READY, "W of a requested pair is not available");
+    CK(cudaMemcpy(w + (long long)k * ctx->ng, ctx->W + (long long)slot * ctx->ng, ctx->ng * sizeof(double),
+                  cudaMemcpyDeviceToHost));
+  }
+  return SBSE_OK;
+}
+
+int sbse_set_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, const double *w) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (!pi || !pj || !w || n_pairs < 1) return fail(ctx, SBSE_ERR_INVALID_ARG, "pairs or w missing");
+  std::vector<int> slots(n_pairs);
+  for (int k = 0; k < n_pairs; ++k) {
+    if (pi[k] < 0 || pj[k] < pi[k] || pj[k] >= ctx->n_o)
+      return fail(ctx, SBSE_ERR_INVALID_ARG, "pair indices must satisfy 0 <= i <= j < n_o");
+    slots[k] = pair_index(ctx->n_o, pi[k], pj[k]);
+  }
+  const long long tot = (long long)n_pairs * ctx->ng;
+  for (long long i = 0; i < tot; ++i)
+    if (!isfinite(w[i])) return fail(ctx, SBSE_ERR_NUMERIC, "w has NaN or Inf");
+  CK(cudaSetDevice(ctx->device));
+  for (int k = 0; k < n_pairs; ++k) {
+    CK(cudaMemcpyAsync(ctx->W + (long long)slots[k] * ctx->ng, w + (long long)k * ctx->ng,
+                       ctx->ng * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->have[slots[k]] = 1;
+  }
+  ctx->have_A = false;
+  CK(cudaStreamSynchronize(ctx->stream));
   return SBSE_OK;
 }
 
