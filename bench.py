@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--chunk-mb", type=int, default=None, help="SBSE_OPT_CHUNK_MB (L2 chunking)")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -298,6 +300,53 @@ def main():
     torch.cuda.synchronize()
     a_build_ms = ta0.elapsed_time(ta1)
 
+    # the plain FP64 GPU path on the same workload (shortened propagation, scaled to n_steps):
+    # the comparator of the mixed path
+    fp64 = None
+    if prec == B.SBSE_MIXED and not args.no_fp64_compare:
+        short = max(20, n_steps // 10)
+        prm64 = B.TDHParams(n_s=pre.n_s, n_steps=short, clean_every=pre.clean_every, dt=pre.dt,
+                            gamma=pre.gamma, alpha=pre.alpha, seed=prm.seed)
+        with B.Context(local, B.SBSE_FP64) as c64:
+            c64.set_grid(pre.N, pre.box, system.v_loc)
+            c64.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi, eps, pre.scissor)
+            c64.apply_W(prm64, pairs)
+            ext64 = torch.cuda.ExternalStream(B.sbse_get_stream(c64.h), device=dev)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(ext64)
+            c64.apply_W(prm64, pairs)
+            f1.record(ext64)
+            torch.cuda.synchronize()
+            ms64 = f0.elapsed_time(f1) * n_steps / short
+        fp64 = {"value": P / (ms64 / 1e3), "unit": "W-applications/s",
+                "sample": f"all {P} pairs x {short} TDH steps, scaled to {n_steps}",
+                "mixed_speedup": (P / (ms_step / 1e3)) / (P / (ms64 / 1e3))}
+
+    # learned form: FNO surrogate of the workload's shape (64^3, width 32, 12 modes, 4 layers)
+    surrogate = None
+    if not args.no_surrogate:
+        net = B.FNO(64, width=32, modes=12, layers=4, max_batch=4, device=local)
+        rng = np.random.default_rng(0)
+        net.set_params(0.01 * rng.standard_normal(net.n_params).astype(np.float32))
+        xs = torch.randn((4, 2, 64 ** 3), device=dev)
+        ys = torch.empty((4, 64 ** 3), device=dev)
+        net.forward(4, xs.data_ptr(), ys.data_ptr())
+        net.train_step(4, xs.data_ptr(), ys.data_ptr(), 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            net.forward(4, xs.data_ptr(), ys.data_ptr())
+        t_inf = (time.perf_counter() - t0) / 12
+        t0 = time.perf_counter()
+        for _ in range(3):
+            net.train_step(4, xs.data_ptr(), ys.data_ptr(), 1e-4)
+        t_tr = (time.perf_counter() - t0) / 12
+        net.close()
+        surrogate = {"network": "FNO 64^3, width 32, 12 modes/axis, 4 Fourier layers, BF16 weights",
+                     "infer_ms_per_pair": 1e3 * t_inf, "train_ms_per_pair": 1e3 * t_tr,
+                     "tdh_ms_per_pair": ms_step / P}
+
     # end to end through the C ABI: pinned host inputs -> excitons on the host, every step
     e2e_steps = args.e2e_steps or max(1, min(args.steps, 2))
     v_pin = torch.from_numpy(np.ascontiguousarray(system.v_loc)).pin_memory()
@@ -350,6 +399,8 @@ def main():
         "a_build_ms": a_build_ms,
         "phase_ms_per_step": {str(k): v[0] / args.steps for k, v in phase.items()},
         "excitons_ha": [float(x) for x in ev],
+        "fp64_gpu_path": fp64,
+        "surrogate": surrogate,
         "cpu_baseline": cpu,
     }
     if rank == 0:
