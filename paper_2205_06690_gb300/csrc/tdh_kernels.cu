@@ -666,14 +666,10 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
     count_launch(1);
     launch_reduce_cols(part, (int)chunks, n_cols * n_occ * 2, dV, ov, s);
   }
-  if (use_tc && sizeof(T) == sizeof(float)) {
-    launch_umma_clean_update(ov, n_cols, reinterpret_cast<const float *>(phi_occ), n_occ, g.ng,
-                             reinterpret_cast<float *>(d), reinterpret_cast<const float *>(a), L, npart, err, s);
-    launch_reduce_cols(npart, (int)umma_clean_update_tiles(g.ng), n_cols * 2, dV, sums, s);
-  } else {
-    k_clean_update2<T><<<(unsigned)ptb, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
-    launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
-  }
+  // the projection update stays on the CUDA cores: a tensor-core version (D = O phi^T in tensor memory)
+  // was measured slower because its epilogue's read-modify-write of d cannot be coalesced
+  k_clean_update2<T><<<(unsigned)ptb, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
+  launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
   k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
   dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
   k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);
