@@ -46,6 +46,8 @@ struct sbse_ctx {
   int device = 0;
   int precision = SBSE_FP64;
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;  // eta0 propagation, concurrent with the pair batch
+  cudaEvent_t ev_start = nullptr, ev_a = nullptr;
   std::string err;
   // grid
   int N = 0;
@@ -296,20 +298,27 @@ template <> const double *phi_T<double>(sbse_ctx *ctx) { return ctx->phi64; }
 // forward 3D FFT with the fused pre-operation, the z multiplier, and the inverse 3D FFT of the
 // orbitals of fa (n_items contiguous fields in `data`); the epilogue writes the induced density of
 // every pair (dens != null, L orbitals per pair) or just stores the propagated orbitals
+enum RoundTripParts { RT_FWD_Z = 1, RT_INV = 2, RT_ALL = 3 };
+
 template <typename T>
 void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T> &fa, C2<T> *data,
-                         int n_items, const C2<T> *a_next, int L, T *dens) {
-  cudaStream_t st = ctx->stream;
+                         int n_items, const C2<T> *a_next, int L, T *dens, cudaStream_t st = nullptr,
+                         int parts = RT_ALL) {
+  if (!st) st = ctx->stream;
   if (fast_supported<T>(g.N)) {
-    launch_plane_fwd<T>(g, fa, st);
-    launch_zcol<T>(g, data, n_items, Z_KINETIC, st);
-    launch_plane_inv_orb<T>(g, data, n_items, a_next, L, dens, st);
+    if (parts & RT_FWD_Z) {
+      launch_plane_fwd<T>(g, fa, st);
+      launch_zcol<T>(g, data, n_items, Z_KINETIC, st);
+    }
+    if (parts & RT_INV) launch_plane_inv_orb<T>(g, data, n_items, a_next, L, dens, st);
   } else {
-    launch_xfwd<T>(g, fa, st);
-    launch_ypass<T>(g, data, n_items, -1, st);
-    launch_zpass<T>(g, data, n_items, Z_KINETIC, st);
-    launch_ypass<T>(g, data, n_items, +1, st);
-    launch_xinv_orb<T>(g, data, n_items, a_next, L, dens, st);
+    if (parts & RT_FWD_Z) {
+      launch_xfwd<T>(g, fa, st);
+      launch_ypass<T>(g, data, n_items, -1, st);
+      launch_zpass<T>(g, data, n_items, Z_KINETIC, st);
+      launch_ypass<T>(g, data, n_items, +1, st);
+    }
+    if (parts & RT_INV) launch_xinv_orb<T>(g, data, n_items, a_next, L, dens, st);
   }
 }
 
@@ -554,9 +563,13 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       clk_end(ctx, c0);
       goto poisson_step;
     }
-    round_trip_orbitals<T>(ctx, g, xa, anext, L, nullptr, L, nullptr);
-    // the three passes run over chunks of pairs small enough to stay in L2 between the passes,
-    // so that each orbital crosses HBM about once per step instead of three times
+    // the eta0 set (small launches) runs on the auxiliary stream, concurrently with the first two
+    // passes of the pair batch; the pairs' inverse pass (which needs the new eta0) waits for it
+    CK(cudaEventRecord(ctx->ev_start, st));
+    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_start, 0));
+    round_trip_orbitals<T>(ctx, g, xa, anext, L, nullptr, L, nullptr, ctx->aux, RT_ALL);
+    CK(cudaEventRecord(ctx->ev_a, ctx->aux));
+    // the three passes run over chunks of pairs (SBSE_OPT_CHUNK_MB, default: all pairs at once)
     for (int p0 = 0; p0 < P; p0 += chunk_pairs) {
       const int pc = std::min(chunk_pairs, P - p0);
       C *dc = d + (long long)p0 * L * ng;
@@ -569,7 +582,9 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       xb.em1 = em1 ? em1 + (long long)p0 * ng : nullptr;
       xb.L = L;
       xb.pv = pending ? g.pv_dt : g.pv_half;
-      round_trip_orbitals<T>(ctx, g, xb, dc, pc * L, anext, L, dn + (long long)p0 * ng);
+      round_trip_orbitals<T>(ctx, g, xb, dc, pc * L, anext, L, dn + (long long)p0 * ng, st, RT_FWD_Z);
+      if (p0 == 0) CK(cudaStreamWaitEvent(st, ctx->ev_a, 0));
+      round_trip_orbitals<T>(ctx, g, xb, dc, pc * L, anext, L, dn + (long long)p0 * ng, st, RT_INV);
     }
     CHECK_LAUNCH("step");
     clk_end(ctx, c0);
@@ -760,6 +775,9 @@ int sbse_create(sbse_ctx **out, int device, int precision) {
   c->precision = precision;
   if ((e = cudaSetDevice(device)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMalloc((void **)&c->flag, sizeof(int))) != cudaSuccess) {
     g_create_error = std::string("CUDA setup failed: ") + cudaGetErrorString(e);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -786,6 +804,10 @@ void sbse_destroy(sbse_ctx *ctx) {
   free_scratch(ctx);
   dfree(ctx->flag);
   for (auto e : ctx->clk.ev) cudaEventDestroy(e);
+  if (ctx->aux) cudaStreamSynchronize(ctx->aux);
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

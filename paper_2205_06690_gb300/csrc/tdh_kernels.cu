@@ -576,8 +576,9 @@ __global__ void __launch_bounds__(256)
         Os[cc][ss] = v;
       }
       __syncthreads();
-      const int smax = (n_occ - st0) < kUpS ? (n_occ - st0) : kUpS;
-      for (int ss = 0; ss < smax; ++ss) {
+      // the tiles are zero-padded beyond n_occ, so the full (unrolled) tile can be swept
+#pragma unroll 16
+      for (int ss = 0; ss < kUpS; ++ss) {
         T p[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) p[j] = Ph[ss][tp * 4 + j];
