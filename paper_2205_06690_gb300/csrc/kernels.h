@@ -148,6 +148,13 @@ int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const floa
                               long long ng, double scale, double *out, double *work, int *err,
                               cudaStream_t s);
 
+// cleaning update on the tensor cores: d_c -= sum_s O[2c+h][s] phi_s (h = re / im parts), plus
+// per-tile norm partials npart[tile][c][2] (tiles of umma_clean_update_tiles(ng) rows)
+void launch_umma_clean_update(const double *ov, int n_cols, const float *phi, int n_occ, long long ng,
+                              float *d_interleaved, const float *a_interleaved, int L, double *npart, int *err,
+                              cudaStream_t s);
+long long umma_clean_update_tiles(long long ng);
+
 // ---- eigensolver (eig.cu)
 int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, cudaStream_t s);
 size_t eig_work_bytes(int n);

@@ -335,24 +335,38 @@ void launch_init_a(const GridTables<T> &g, const double *phi, int n_occ, const d
   count_launch(1);
 }
 
-// out[c] = scale * sum_{row < rows} part[row][c]  (fixed order: deterministic)
-__global__ void k_reduce_cols(const double *part, int rows, int cols, double scale, double *out) {
-  __shared__ double red[256];
-  const int c = blockIdx.x;
-  double s = 0.0;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) s += part[(long long)r * cols + c];
-  red[threadIdx.x] = s;
+// out[c] = scale * sum_{row < rows} part[row][c]  (fixed order: deterministic). A block owns 8
+// adjacent columns; its 32 row groups read rows g, g + 32, ... (8 consecutive doubles per row and
+// group: 64-byte segments) and are combined by a fixed tree in shared memory.
+constexpr int kRcCols = 8, kRcGroups = 32;
+__global__ void __launch_bounds__(kRcCols * kRcGroups)
+    k_reduce_cols(const double *part, int rows, int cols, double scale, double *out) {
+  __shared__ double red[kRcGroups][kRcCols];
+  const int cx = threadIdx.x % kRcCols, g = threadIdx.x / kRcCols;
+  const int c = blockIdx.x * kRcCols + cx;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (c < cols) {
+    int r = g;
+    for (; r + 3 * kRcGroups < rows; r += 4 * kRcGroups) {
+      s0 += part[(long long)r * cols + c];
+      s1 += part[(long long)(r + kRcGroups) * cols + c];
+      s2 += part[(long long)(r + 2 * kRcGroups) * cols + c];
+      s3 += part[(long long)(r + 3 * kRcGroups) * cols + c];
+    }
+    for (; r < rows; r += kRcGroups) s0 += part[(long long)r * cols + c];
+  }
+  red[g][cx] = (s0 + s1) + (s2 + s3);
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+  for (int w = kRcGroups / 2; w > 0; w >>= 1) {
+    if (g < w) red[g][cx] += red[g + w][cx];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[c] = scale * red[0];
+  if (g == 0 && c < cols) out[c] = scale * red[0][cx];
 }
 
 void launch_reduce_cols(const double *part, int rows, int cols, double scale, double *out,
                         cudaStream_t s) {
-  if (cols > 0) k_reduce_cols<<<cols, 256, 0, s>>>(part, rows, cols, scale, out);
+  if (cols > 0) k_reduce_cols<<<(cols + kRcCols - 1) / kRcCols, kRcCols * kRcGroups, 0, s>>>(part, rows, cols, scale, out);
   count_launch(1);
 }
 
@@ -596,7 +610,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int c = cg0 + tcg * 4 + i;
-      double v1 = 0.0, v2 = 0.0;
+      // sums in T over the block's 128 points (FP64 per-point work would saturate this GPU's
+      // narrow FP64 pipe); FP64 from the per-tile partials on
+      T v1 = T(0), v2 = T(0);
       if (c < n_cols) {
         C *dp = d + (long long)c * ng + r0 + tp * 4;
         const C *ap = a + (long long)(c % L) * ng + r0 + tp * 4;
@@ -608,8 +624,8 @@ __global__ void __launch_bounds__(256)
             dv.y -= acc[i][j].y;
             dp[j] = dv;
             const C a0 = ap[j];
-            v1 += 2.0 * ((double)a0.x * dv.x + (double)a0.y * dv.y);
-            v2 += (double)dv.x * dv.x + (double)dv.y * dv.y;
+            v1 += T(2) * (a0.x * dv.x + a0.y * dv.y);
+            v2 += dv.x * dv.x + dv.y * dv.y;
           }
         }
       }
@@ -619,8 +635,8 @@ __global__ void __launch_bounds__(256)
         v2 += __shfl_xor_sync(0xffffffffu, v2, o);
       }
       if (tp == 0 && c < n_cols) {
-        npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = v1;
-        npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = v2;
+        npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = (double)v1;
+        npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = (double)v2;
       }
     }
   }
@@ -667,10 +683,14 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
     count_launch(1);
     launch_reduce_cols(part, (int)chunks, n_cols * n_occ * 2, dV, ov, s);
   }
-  // the projection update stays on the CUDA cores: a tensor-core version (D = O phi^T in tensor memory)
-  // was measured slower because its epilogue's read-modify-write of d cannot be coalesced
-  k_clean_update2<T><<<(unsigned)ptb, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
-  launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
+  if (use_tc && sizeof(T) == sizeof(float)) {
+    launch_umma_clean_update(ov, n_cols, reinterpret_cast<const float *>(phi_occ), n_occ, g.ng,
+                             reinterpret_cast<float *>(d), reinterpret_cast<const float *>(a), L, npart, err, s);
+    launch_reduce_cols(npart, (int)umma_clean_update_tiles(g.ng), n_cols * 2, dV, sums, s);
+  } else {
+    k_clean_update2<T><<<(unsigned)ptb, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
+    launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
+  }
   k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
   dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
   k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);

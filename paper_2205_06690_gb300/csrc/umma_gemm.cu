@@ -287,6 +287,189 @@ __global__ void __launch_bounds__(kUmThreads)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
+// ---- cleaning projection update on the tensor cores ------------------------------------------
+// d_c(r) -= sum_s O[c][s] phi_s(r) (Eq. 15) as D[m][r] = sum_s O[m][s] phi_s(r) with m = 2c + h the
+// real / imaginary row of column c; A = O (128 rows per tile), B = phi^T (256 grid points per tile,
+// transposed into the K-major layout by the producer), K = the occupied states in stages of 64.
+// The epilogue subtracts D from d in place (coalesced through shared memory) and writes per-tile
+// partial sums of 2 Re(conj(eta0) d) and |d|^2 per column for the renormalisation.
+constexpr int kCuN = 256;
+
+__global__ void __launch_bounds__(kUmThreads)
+    k_umma_clean_update(const double *ov, int M, const float *phi, int n_occ, long long ng, float *d,
+                        const float *a, int L, double *npart, int *err) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  uint8_t *a_hi = smem, *a_lo = a_hi + kUmM * kUmBK * 2;
+  uint8_t *b_hi = a_lo + kUmM * kUmBK * 2, *b_lo = b_hi + kCuN * kUmBK * 2;
+  const int m0 = blockIdx.y * kUmM;
+  const long long r0 = (long long)blockIdx.x * kCuN;
+  const int n_cols = M / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kCuN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = make_idesc(kUmM, kCuN);
+  const int n_iter = (n_occ + kUmBK - 1) / kUmBK;
+  bool ok = true;
+  for (int it = 0; it < n_iter; ++it) {
+    const int s0 = it * kUmBK;
+    bool w = true;
+    if (it > 0) w = mbar_wait(smem_u32(&mbar), (uint32_t)((it - 1) & 1));
+    if (!__syncthreads_and(w)) {
+      ok = false;
+      break;
+    }
+    // A: O rows (FP64) -> BF16 hi / lo; unit = 8 rows x 32 states
+    for (int u = warp; u < (kUmM / 8) * 2; u += kUmThreads / 32) {
+      const int row = (u >> 1) * 8 + (lane & 7);
+      const int kc = (u & 1) * 4 + (lane >> 3);
+      const int m = m0 + row;
+      float x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int sidx = s0 + kc * 8 + j;
+        x[j] = (m < M && sidx < n_occ) ? (float)ov[(long long)m * n_occ + sidx] : 0.f;
+      }
+      uint4 hi, lo;
+      split8(x, &hi, &lo);
+      *reinterpret_cast<uint4 *>(a_hi + canon_off(row, kc)) = hi;
+      *reinterpret_cast<uint4 *>(a_lo + canon_off(row, kc)) = lo;
+    }
+    // B: phi^T, row = grid point, k = state; unit = 32 points x 8 states, lane = point
+    for (int u = warp; u < (kCuN / 32) * (kUmBK / 8); u += kUmThreads / 32) {
+      const int row = (u % (kCuN / 32)) * 32 + lane;
+      const int kc = u / (kCuN / 32);
+      const long long r = r0 + row;
+      float x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int sidx = s0 + kc * 8 + j;
+        x[j] = (r < ng && sidx < n_occ) ? phi[(long long)sidx * ng + r] : 0.f;
+      }
+      uint4 hi, lo;
+      split8(x, &hi, &lo);
+      *reinterpret_cast<uint4 *>(b_hi + canon_off(row, kc)) = hi;
+      *reinterpret_cast<uint4 *>(b_lo + canon_off(row, kc)) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+      for (int t = 0; t < kUmBK / 16; ++t) {
+        const uint32_t o = t * 256;
+        const uint64_t dah = make_desc(ah + o, 128, 1024), dal = make_desc(al + o, 128, 1024);
+        const uint64_t dbh = make_desc(bh + o, 128, 1024), dbl = make_desc(bl + o, 128, 1024);
+        mma_bf16(tmem, dah, dbh, idesc, (it > 0 || t > 0) ? 1u : 0u);
+        mma_bf16(tmem, dah, dbl, idesc, 1u);
+        mma_bf16(tmem, dal, dbh, idesc, 1u);
+      }
+      mma_commit(smem_u32(&mbar));
+    }
+  }
+  if (ok && n_iter > 0) ok = __syncthreads_and(mbar_wait(smem_u32(&mbar), (uint32_t)((n_iter - 1) & 1)));
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    mbar_wait(smem_u32(&mbar), (uint32_t)((n_iter - 1) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  // Epilogue, in two halves of 128 grid points: the accumulator rows (m = 2c + h) are staged in the
+  // (now free) operand shared memory with a padded stride, then every warp updates whole complex
+  // columns with coalesced float2 accesses and reduces their norm sums.
+  constexpr int kHalf = 128, kLd = kHalf + 1;
+  float *Dsm = reinterpret_cast<float *>(smem);  // kUmM x kLd floats (66 KB) inside the operand buffer
+  __shared__ double colsum[kUmM / 2][2];
+  for (int i = threadIdx.x; i < kUmM; i += blockDim.x) colsum[i >> 1][i & 1] = 0.0;
+  const int c0 = m0 / 2;
+  for (int half = 0; half < kCuN / kHalf && ok; ++half) {
+    __syncthreads();
+    for (int cc = 0; cc < kHalf; cc += 16) {
+      uint32_t rr[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * kHalf + cc);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+            "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float *row = Dsm + (warp * 32 + lane) * kLd + cc;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) row[j] = __uint_as_float(rr[j]);
+    }
+    __syncthreads();
+    for (int cl = warp; cl < kUmM / 2; cl += kUmThreads / 32) {
+      const int c = c0 + cl;
+      if (c >= n_cols) continue;
+      float2 *dc = reinterpret_cast<float2 *>(d) + (long long)c * ng;
+      const float2 *ac = reinterpret_cast<const float2 *>(a) + (long long)(c % L) * ng;
+      // FP32 sums over the 128 points of the half (the FP64 pipe of this GPU is too slow for
+      // per-point work); they are carried on in FP64 per tile and across tiles
+      float v1 = 0.f, v2 = 0.f;
+#pragma unroll
+      for (int p = lane; p < kHalf; p += 32) {
+        const long long r = r0 + half * kHalf + p;
+        if (r < ng) {
+          float2 dv = dc[r];
+          dv.x -= Dsm[(2 * cl) * kLd + p];
+          dv.y -= Dsm[(2 * cl + 1) * kLd + p];
+          dc[r] = dv;
+          const float2 a0 = ac[r];
+          v1 += 2.f * (a0.x * dv.x + a0.y * dv.y);
+          v2 += dv.x * dv.x + dv.y * dv.y;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+      }
+      if (lane == 0) {
+        colsum[cl][0] += (double)v1;
+        colsum[cl][1] += (double)v2;
+      }
+    }
+  }
+  __syncthreads();
+  for (int cl = threadIdx.x; cl < kUmM / 2; cl += blockDim.x) {
+    const int c = c0 + cl;
+    if (ok && c < n_cols) {
+      npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = colsum[cl][0];
+      npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = colsum[cl][1];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCuN));
+}
+
+// grid-point tiles of the tensor-core cleaning update (rows of its norm partials)
+long long umma_clean_update_tiles(long long ng) { return (ng + kCuN - 1) / kCuN; }
+
+void launch_umma_clean_update(const double *ov, int n_cols, const float *phi, int n_occ, long long ng,
+                              float *d_interleaved, const float *a_interleaved, int L, double *npart, int *err,
+                              cudaStream_t s) {
+  const int M = 2 * n_cols;
+  const size_t smem = (size_t)2 * (kUmM + kCuN) * kUmBK * 2;
+  cudaFuncSetAttribute(k_umma_clean_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)umma_clean_update_tiles(ng), (M + kUmM - 1) / kUmM);
+  k_umma_clean_update<<<grid, kUmThreads, smem, s>>>(ov, M, phi, n_occ, ng, d_interleaved, a_interleaved, L,
+                                                     npart, err);
+  count_launch(1);
+}
+
 // tile width for Nn output columns: multiple of 16, at most 256
 static int umma_nt(int Nn) {
   int nt = ((Nn + 15) / 16) * 16;
