@@ -103,9 +103,40 @@ __device__ __forceinline__ void fwd_planes(const GView<T> &g, const XfwdArgs<T> 
       }
     }
   } else {
-    for (int l = threadIdx.x; l < PPB * NN; l += NT) {
-      const int pl = l / NN, rem = l - pl * NN, y = rem / N, x = rem - y * N;
-      S[(pl * N + y) * LD + x] = preop_at<T>(g, it, off + l);
+    // the other pre-operations, with the mode resolved outside the point loop so that each batch
+    // of UB points issues all its loads before the first shared-memory store
+    constexpr int UB = 8;
+    auto run = [&](auto f) {
+#pragma unroll
+      for (int k0 = 0; k0 < N; k0 += UB) {
+        C v[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k)
+          if (k0 + k < N) v[k] = f(off + threadIdx.x + (k0 + k) * NT);
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          if (k0 + k < N) {
+            const int l = threadIdx.x + (k0 + k) * NT;
+            const int pl = l / NN, rem = l - pl * NN, y = rem / N, x = rem - y * N;
+            S[(pl * N + y) * LD + x] = v[k];
+          }
+        }
+      }
+    };
+    if (it.mode == XF_PHASE_A) {
+      run([&](long long i) { return cmul(it.pv[i], it.in[i]); });
+    } else if (it.mode == XF_PACK_DN) {
+      if (it.r1)
+        run([&](long long i) { return C{it.r0[i], it.r1[i]}; });
+      else
+        run([&](long long i) { return C{it.r0[i], T(0)}; });
+    } else if (it.mode == XF_PACK_PROD) {
+      if (it.r2)
+        run([&](long long i) { return C{it.r0[i] * it.r1[i], it.r2[i] * it.r3[i]}; });
+      else
+        run([&](long long i) { return C{it.r0[i] * it.r1[i], T(0)}; });
+    } else {
+      run([&](long long i) { return preop_at<T>(g, it, i); });
     }
   }
   __syncthreads();
@@ -290,21 +321,38 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
   }
   C *base = data + item * g.ng + off;
   plane_inverse<T, N>(S, base, pl, q);
-#pragma unroll 4
-  for (int k = 0; k < N; ++k) {
-    const int l = threadIdx.x + k * NT;
-    const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
-    const C v = S[(p * N + y) * LD + x];
-    {
+  // Poisson epilogue: unpack the two real potentials of the item, store u, accumulate the damped
+  // time integral and store E - 1; the accumulator loads of a batch are issued together
+  const T coef = (T)pa.po.coef, tau = (T)pa.po.tau_next;
+  const bool keep = pa.po.keep != 0.0;
+  const int n_h = (2 * item + 1 < pa.po.n_out) ? 2 : 1;
+  constexpr int UB = 8;
+#pragma unroll 2
+  for (int k0 = 0; k0 < N; k0 += UB) {
+    C v[UB];
+    T old[UB][2];
+#pragma unroll
+    for (int k = 0; k < UB; ++k) {
+      if (k0 + k >= N) break;
+      const int l = threadIdx.x + (k0 + k) * NT;
+      const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
+      v[k] = S[(p * N + y) * LD + x];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        old[k][h] = (acc && keep && h < n_h) ? acc[(2 * item + h) * g.ng + off + l] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < UB; ++k) {
+      if (k0 + k >= N) break;
+      const int l = threadIdx.x + (k0 + k) * NT;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const long long kk = 2 * item + h;
-        if (kk >= pa.po.n_out) break;
-        const T val = h ? v.y : v.x;
-        const long long o = kk * g.ng + off + l;
+        if (h >= n_h) break;
+        const T val = h ? v[k].y : v[k].x;
+        const long long o = (2 * item + h) * g.ng + off + l;
         if (u_out) u_out[o] = val;
-        if (acc) acc[o] = (pa.po.keep != 0.0) ? acc[o] + (T)pa.po.coef * val : (T)pa.po.coef * val;
-        if (em1_out) em1_out[o] = phase_em1<T>(val, (T)pa.po.tau_next);
+        if (acc) acc[o] = old[k][h] + coef * val;
+        if (em1_out) em1_out[o] = phase_em1<T>(val, tau);
       }
     }
   }
