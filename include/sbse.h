@@ -196,6 +196,11 @@ int sbse_get_stream(const sbse_ctx *ctx, void **stream);
  * register-pencil FFT); 0 uses three separate pass kernels, which are faster on GB300 (the merged
  * kernel is register-limited to fewer resident warps). Results do not depend on it. */
 #define SBSE_OPT_PERSISTENT 3
+/* SBSE_OPT_TMA_PLANES (default 1): in SBSE_MIXED on grids of 32, 40, 48 or 64 points per axis, the
+ * inverse plane pass of the pair batch (with the induced density of Eq. 11) runs as a persistent
+ * kernel fed by bulk asynchronous copies (TMA) of the next orbital's planes; 0 uses the plain plane
+ * kernel. Results do not depend on it. */
+#define SBSE_OPT_TMA_PLANES 4
 int sbse_set_option(sbse_ctx *ctx, int option, int value);
 
 /* Number of CUDA kernel launches the library has issued in this process (all contexts), for

@@ -35,6 +35,7 @@ SBSE_DIRECT = 2
 SBSE_OPT_TENSOR_CORES = 1
 SBSE_OPT_CHUNK_MB = 2
 SBSE_OPT_PERSISTENT = 3
+SBSE_OPT_TMA_PLANES = 4
 
 _ERR_NAMES = {v: k for k, v in globals().items() if k.startswith("SBSE_ERR_")}
 

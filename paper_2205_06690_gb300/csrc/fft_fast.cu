@@ -16,6 +16,7 @@
 #include "fft_reg.cuh"
 #include "kernels.h"
 #include "passes.cuh"
+#include "tma.cuh"
 
 namespace sbse {
 
@@ -359,6 +360,171 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
 }
 
 // ------------------------------------------------------------------------------------------
+// Inverse plane pass of the pair batch with the induced density, streamed by bulk copies (TMA):
+// a persistent block walks its (pair, plane group) units and, inside each, the L orbitals; the PPB
+// contiguous planes of the next orbital (and of eta0 at the same planes) are copied into shared
+// memory while the current ones are transformed, so no thread waits on a global load. Per chunk:
+// y inverse FFTs read the staged planes (thread per column, conflict-free) into the padded work
+// tile, which frees the staging buffer for the next chunk's copy; x inverse FFTs in the work tile;
+// the epilogue stores the orbital and accumulates the density from the staged eta0.
+
+// planes per chunk: largest divisor of N with <= 128 threads and <= 112 KB of shared memory
+// (two blocks per SM)
+constexpr int tma_inv_ppb(int N) {
+  int best = 0;
+  for (int d = 1; d <= N; ++d)
+    if (N % d == 0 && d * N <= 128 && (long long)d * N * N * 16 + (long long)d * N * (N + 1) * 8 <= 112 * 1024)
+      best = d;
+  return best;
+}
+template <int N> constexpr size_t tma_inv_smem() {
+  return (size_t)tma_inv_ppb(N) * N * N * 16 + (size_t)tma_inv_ppb(N) * N * (N + 1) * 8;
+}
+// grids streamed this way (even N: every chunk offset is a multiple of 16 bytes)
+constexpr bool tma_inv_size(int N) { return N == 32 || N == 40 || N == 48 || N == 64; }
+
+template <int N>
+__global__ void __launch_bounds__(tma_inv_ppb(N) * N)
+    k_plane_inv_density_tma(GView<float> g, float2 *data, const float2 *a_next, float *dens, int L,
+                            int n_pairs, int *err) {
+  using C = float2;
+  constexpr int PPB = tma_inv_ppb(N), NN = N * N, LD = N + 1, NT = PPB * N, G = N / PPB;
+  constexpr unsigned kChunk = PPB * NN * sizeof(C);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C *Sd = reinterpret_cast<C *>(smem_raw);  // staged orbital planes (dense)
+  C *Sa = Sd + PPB * NN;                     // staged eta0 planes (dense)
+  C *W = Sa + PPB * NN;                      // work tile, rows padded to N + 1
+  __shared__ __align__(8) uint64_t bar_d, bar_a;
+  const long long units = (long long)n_pairs * G;
+  long long u = blockIdx.x;
+  if (u >= units) return;
+  const int pl = threadIdx.x / N, q = threadIdx.x - pl * N;
+  auto src_d = [&](long long uu, int e) {
+    return data + ((uu / G) * L + e) * g.ng + (uu % G) * (long long)(PPB * NN);
+  };
+  auto src_a = [&](long long uu, int e) { return a_next + (long long)e * g.ng + (uu % G) * (long long)(PPB * NN); };
+  if (threadIdx.x == 0) {
+    tma_bar_init(&bar_d, 1);
+    tma_bar_init(&bar_a, 1);
+    tma_bar_expect(&bar_d, kChunk);
+    tma_load_1d(Sd, src_d(u, 0), kChunk, &bar_d);
+    tma_bar_expect(&bar_a, kChunk);
+    tma_load_1d(Sa, src_a(u, 0), kChunk, &bar_a);
+  }
+  __syncthreads();
+  unsigned ph_d = 0, ph_a = 0;
+  bool pend_d = true, pend_a = true, ok = true;
+  int ell = 0;
+  float accd[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) accd[k] = 0.f;
+  while (true) {
+    long long un = u;
+    int en = ell + 1;
+    if (en == L) {
+      en = 0;
+      un += gridDim.x;
+    }
+    const bool has_next = un < units;
+    // y inverse FFTs from the staged planes into the work tile
+    if (!__syncthreads_and(tma_bar_wait(&bar_d, ph_d))) {
+      ok = false;
+      break;
+    }
+    ph_d ^= 1u;
+    pend_d = false;
+    {
+      C v[N];
+#pragma unroll
+      for (int y = 0; y < N; ++y) v[y] = Sd[pl * NN + y * N + q];
+      fft_reg<float, N, +1>(v);
+#pragma unroll
+      for (int y = 0; y < N; ++y) W[(pl * N + y) * LD + q] = v[y];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && has_next) {
+      tma_fence_proxy();
+      tma_bar_expect(&bar_d, kChunk);
+      tma_load_1d(Sd, src_d(un, en), kChunk, &bar_d);
+    }
+    pend_d = has_next;
+    {
+      C v[N];
+      C *row = W + (pl * N + q) * LD;
+#pragma unroll
+      for (int x = 0; x < N; ++x) v[x] = row[x];
+      fft_reg<float, N, +1>(v);
+#pragma unroll
+      for (int x = 0; x < N; ++x) row[x] = v[x];
+    }
+    if (!__syncthreads_and(tma_bar_wait(&bar_a, ph_a))) {
+      ok = false;
+      break;
+    }
+    ph_a ^= 1u;
+    pend_a = false;
+    const long long pair = u / G, off = (u % G) * (long long)(PPB * NN);
+    C *base = data + (pair * L + ell) * g.ng + off;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int l = threadIdx.x + k * NT;
+      const int p = l / NN, rem = l - p * NN, y = rem / N, x = rem - y * N;
+      const C dv = W[(p * N + y) * LD + x];
+      base[l] = dv;
+      const C a0 = Sa[l];
+      accd[k] += 2.f * (2.f * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && has_next) {
+      tma_fence_proxy();
+      tma_bar_expect(&bar_a, kChunk);
+      tma_load_1d(Sa, src_a(un, en), kChunk, &bar_a);
+    }
+    pend_a = has_next;
+    if (ell == L - 1) {
+      float *db = dens + pair * g.ng + off;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        db[threadIdx.x + k * NT] = accd[k];
+        accd[k] = 0.f;
+      }
+    }
+    if (!has_next) break;
+    u = un;
+    ell = en;
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    // copies still in flight must land before the block's shared memory is released
+    if (pend_d) tma_bar_wait(&bar_d, ph_d);
+    if (pend_a) tma_bar_wait(&bar_a, ph_a);
+  }
+}
+
+template <int N>
+static bool inv_density_tma(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L,
+                            float *dens, int *err, cudaStream_t s) {
+  if constexpr (tma_inv_size(N)) {
+    constexpr int PPB = tma_inv_ppb(N);
+    const long long units = (long long)(n_items / L) * (N / PPB);
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plane_inv_density_tma<N>, PPB * N,
+                                                    tma_inv_smem<N>());
+    }
+    if (per_sm < 1 || units < 1) return false;
+    const long long grid = units < (long long)per_sm * sms ? units : (long long)per_sm * sms;
+    k_plane_inv_density_tma<N><<<(unsigned)grid, PPB * N, tma_inv_smem<N>(), s>>>(view(g), d, a_next, dens, L,
+                                                                                  n_items / L, err);
+    return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------------------------------
 // Persistent split-operator step: one launch advances the eta0 set and every pair's L orbitals by
 // one step of Eq. (10) and writes each pair's induced density. Blocks claim tiles from a host-built
 // queue; a tile waits (bounded) for the tiles it reads, whose queue positions are always earlier,
@@ -451,6 +617,9 @@ template <typename T, int N> static void set_attrs() {
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_DENSITY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if constexpr (sizeof(T) == 4 && tma_inv_size(N))
+    cudaFuncSetAttribute(k_plane_inv_density_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tma_inv_smem<N>());
 }
 
 template <typename T> struct FastOps {
@@ -584,7 +753,19 @@ template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_i
 
 template <typename T>
 void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items, const C2<T> *a_next, int L,
-                          T *dens, cudaStream_t s) {
+                          T *dens, cudaStream_t s, int *tma_err) {
+  if constexpr (sizeof(T) == 4) {
+    if (dens && tma_err) {
+      bool done = false;
+#define SBSE_CALL(n) done = inv_density_tma<n>(g, d, n_items, a_next, L, dens, tma_err, s)
+      SBSE_FAST_SWITCH(g.N, SBSE_CALL)
+#undef SBSE_CALL
+      if (done) {
+        count_launch(1);
+        return;
+      }
+    }
+  }
   const int mode = dens ? PI_DENSITY : PI_PLAIN;
   const PoissonOut po{0, 0.0, 0.0, 0.0};
 #define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_items, a_next, L, dens, nullptr, nullptr, nullptr, po, mode, s)
@@ -613,7 +794,7 @@ void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, con
   template void launch_plane_fwd<T>(const GridTables<T> &, const XfwdArgs<T> &, cudaStream_t);     \
   template void launch_zcol<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t);            \
   template void launch_plane_inv_orb<T>(const GridTables<T> &, C2<T> *, int, const C2<T> *, int,   \
-                                        T *, cudaStream_t);                                        \
+                                        T *, cudaStream_t, int *);                                 \
   template void launch_plane_inv_poisson<T>(const GridTables<T> &, C2<T> *, int, const PoissonOut &, \
                                             T *, T *, C2<T> *, cudaStream_t);
 

@@ -52,8 +52,11 @@ template <typename T> struct XfwdArgs {
 template <typename T> void launch_xfwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
 template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
 template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s);
+// tma_err != null (FP32, density epilogue, N in 32 / 40 / 48 / 64): the bulk-copy streamed kernel,
+// which sets *tma_err if one of its bounded waits runs out
 template <typename T> void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items,
-                                                const C2<T> *a_next, int L, T *dens, cudaStream_t s);
+                                                const C2<T> *a_next, int L, T *dens, cudaStream_t s,
+                                                int *tma_err = nullptr);
 // Poisson epilogue outputs of slot pair k: u_out[k] = u, acc[k] (+)= coef u, and, when em1_out is
 // not null, em1_out[k] = exp(-i u tau_next) - 1 = -2i sin(u tau_next/2) exp(-i u tau_next/2), the
 // potential factor of the next split-operator step.

@@ -76,6 +76,8 @@ struct sbse_ctx {
   int tensor_cores = 1;
   // split-operator step as one persistent kernel (SBSE_OPT_PERSISTENT)
   int persistent = 0;
+  // inverse plane pass of the pair batch streamed by bulk copies (SBSE_OPT_TMA_PLANES)
+  int tma_planes = 1;
   // bytes of propagated orbitals per chunk of pairs (SBSE_OPT_CHUNK_MB); 0 = all pairs at once
   double l2_chunk_bytes = 1e30;
   // profiling
@@ -310,7 +312,8 @@ void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T
       launch_plane_fwd<T>(g, fa, st);
       launch_zcol<T>(g, data, n_items, Z_KINETIC, st);
     }
-    if (parts & RT_INV) launch_plane_inv_orb<T>(g, data, n_items, a_next, L, dens, st);
+    if (parts & RT_INV)
+      launch_plane_inv_orb<T>(g, data, n_items, a_next, L, dens, st, ctx->tma_planes ? ctx->flag : nullptr);
   } else {
     if (parts & RT_FWD_Z) {
       launch_xfwd<T>(g, fa, st);
@@ -1052,6 +1055,10 @@ int sbse_set_option(sbse_ctx *ctx, int option, int value) {
   }
   if (option == SBSE_OPT_PERSISTENT) {
     ctx->persistent = value != 0;
+    return SBSE_OK;
+  }
+  if (option == SBSE_OPT_TMA_PLANES) {
+    ctx->tma_planes = value != 0;
     return SBSE_OK;
   }
   if (option == SBSE_OPT_CHUNK_MB) {

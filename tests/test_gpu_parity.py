@@ -244,3 +244,31 @@ def test_persistent_step_matches_pass_kernels(B, mid48, prec):
                            p.scissor)
             out.append(c.apply_W(prm, tdh.pair_list(p.n_o)[3:10], copy_out=True))
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("N,box", [(32, 10.0), (40, 12.0), (64, 16.0)])
+def test_tma_streamed_inverse_pass_matches_plain_kernel(B, N, box):
+    """The inverse plane pass fed by bulk asynchronous copies (SBSE_OPT_TMA_PLANES, mixed mode) runs
+    the same transforms and density sums as the plain plane kernel: W agrees to FP32 round-off. Odd
+    pair count (5) and L = 3, so that the persistent grid's last units are uneven; on 32^3 and 40^3
+    W also matches the FP64 oracle within the mixed tolerance."""
+    n_occ, n_o, n_c = 6, 3, 4
+    s = _small_system(N, box, 5, N, n_occ, n_o, n_c)
+    prm = B.TDHParams(n_s=3, n_steps=24, clean_every=10, dt=0.05, gamma=0.1, alpha=1e-4, seed=2)
+    pairs = tdh.pair_list(n_o)[:5]
+    out = []
+    for tma in (0, 1):
+        with B.Context(0, B.SBSE_MIXED) as c:
+            B.sbse_set_option(c.h, B.SBSE_OPT_TMA_PLANES, tma)
+            c.set_grid(s.N, s.box, s.v_loc)
+            c.set_orbitals(n_occ, n_o, n_c, s.phi[:n_occ + n_c], s.eps[:n_occ + n_c], 0.5)
+            out.append(c.apply_W(prm, pairs, copy_out=True))
+    assert rel_err(out[1], out[0]) < 1e-6
+    if N <= 40:
+        coeff = tdh.stochastic_coefficients(prm.seed, prm.n_s, n_occ, "gaussian")
+        op = tdh.TDHParams(n_steps=prm.n_steps, dt=prm.dt, gamma=prm.gamma, alpha=prm.alpha,
+                           clean_every=prm.clean_every)
+        ref = tdh.screened_potentials(tdh.Grid(N, box), s.v_loc, s.phi, n_occ, n_o, coeff, op,
+                                      pairs=pairs)
+        for k, pr in enumerate(pairs):
+            assert rel_err(out[1][k].reshape(N, N, N), ref[pr]) < 2e-3
