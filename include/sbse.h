@@ -197,9 +197,9 @@ int sbse_get_stream(const sbse_ctx *ctx, void **stream);
  * kernel is register-limited to fewer resident warps). Results do not depend on it. */
 #define SBSE_OPT_PERSISTENT 3
 /* SBSE_OPT_TMA_PLANES (default 1): in SBSE_MIXED on grids of 32, 40, 48 or 64 points per axis, the
- * inverse plane pass of the pair batch (with the induced density of Eq. 11) runs as a persistent
- * kernel fed by bulk asynchronous copies (TMA) of the next orbital's planes; 0 uses the plain plane
- * kernel. Results do not depend on it. */
+ * inverse plane pass of the pair batch (with the induced density of Eq. 11) and the z-column passes
+ * run as persistent kernels fed by bulk asynchronous copies (TMA) of their next planes or column
+ * slabs; 0 uses the plain pass kernels. Results do not depend on it. */
 #define SBSE_OPT_TMA_PLANES 4
 int sbse_set_option(sbse_ctx *ctx, int option, int value);
 

@@ -501,6 +501,109 @@ __global__ void __launch_bounds__(tma_inv_ppb(N) * N)
   }
 }
 
+// z-column pass streamed by bulk copies: a persistent block walks (item, slab of Y rows) units;
+// the slab's N z-rows (Y N contiguous points each) are copied into shared memory, every thread takes
+// its column (conflict-free across x) into registers, the buffer is refilled with the next unit,
+// and the forward z FFT, the multiplier and the inverse z FFT run while the copies are in flight.
+constexpr int tma_z_rows(int N) {
+  int best = 0;
+  for (int y = 1; y <= N; ++y)
+    if (N % y == 0 && y * N <= 256 && (long long)y * N * N * 8 <= 80 * 1024) best = y;
+  return best;
+}
+
+template <int N>
+__global__ void __launch_bounds__(tma_z_rows(N) * N)
+    k_zcol_tma(GView<float> g, float2 *data, long long n_items, int mult, int *err) {
+  using C = float2;
+  constexpr int Y = tma_z_rows(N), NN = N * N, G = N / Y;
+  constexpr unsigned kRow = Y * N * sizeof(C);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);  // [z][y][x] of the slab
+  __shared__ __align__(8) uint64_t bar;
+  const long long units = n_items * G;
+  long long u = blockIdx.x;
+  if (u >= units) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int yy = threadIdx.x / N, x = threadIdx.x - yy * N;
+  auto issue = [&](long long uu) {  // warp 0: one arrival with the byte count, then N row copies
+    const C *src = data + (uu / G) * g.ng + (uu % G) * (long long)(Y * N);
+    if (lane == 0) tma_bar_expect(&bar, kRow * N);
+    __syncwarp();
+    for (int z = lane; z < N; z += 32) tma_load_1d(S + z * Y * N, src + (long long)z * NN, kRow, &bar);
+  };
+  if (threadIdx.x == 0) tma_bar_init(&bar, 1);
+  __syncthreads();
+  if (warp == 0) issue(u);
+  unsigned ph = 0;
+  bool pend = true, ok = true;
+  const float inv_ng = 1.f / (float)(N * N * N);
+  while (true) {
+    const long long un = u + gridDim.x;
+    const bool has_next = un < units;
+    if (!__syncthreads_and(tma_bar_wait(&bar, ph))) {
+      ok = false;
+      break;
+    }
+    ph ^= 1u;
+    pend = false;
+    C v[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = S[(z * Y + yy) * N + x];
+    __syncthreads();
+    if (warp == 0 && has_next) {
+      tma_fence_proxy();
+      issue(un);
+    }
+    pend = has_next;
+    const int y = (int)(u % G) * Y + yy;
+    fft_reg<float, N, -1>(v);
+    if (mult == Z_KINETIC) {
+      const C mxy = cscale(cmul(g.kin[x], g.kin[y]), inv_ng);
+#pragma unroll
+      for (int z = 0; z < N; ++z) v[z] = cmul(v[z], cmul(mxy, g.kin[z]));
+    } else {
+      const float gxy = g.k2[x] + g.k2[y];
+#pragma unroll
+      for (int z = 0; z < N; ++z) {
+        const float G2 = gxy + g.k2[z];
+        v[z] = cscale(v[z], G2 > 0.f ? float(4.0 * M_PI) * inv_ng / G2 : 0.f);
+      }
+    }
+    fft_reg<float, N, +1>(v);
+    C *base = data + (u / G) * g.ng + (long long)y * N + x;
+#pragma unroll
+    for (int z = 0; z < N; ++z) base[(long long)z * NN] = v[z];
+    if (!has_next) break;
+    u = un;
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    if (pend) tma_bar_wait(&bar, ph);
+  }
+}
+
+template <int N>
+static bool zcol_tma(const GridTables<float> &g, float2 *d, int n_items, int mult, int *err, cudaStream_t s) {
+  if constexpr (tma_inv_size(N)) {
+    constexpr int Y = tma_z_rows(N);
+    constexpr size_t sm = (size_t)Y * N * N * sizeof(float2);
+    const long long units = (long long)n_items * (N / Y);
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zcol_tma<N>, Y * N, sm);
+    }
+    if (per_sm < 1 || units < 1) return false;
+    const long long grid = units < (long long)per_sm * sms ? units : (long long)per_sm * sms;
+    k_zcol_tma<N><<<(unsigned)grid, Y * N, sm, s>>>(view(g), d, n_items, mult, err);
+    return true;
+  }
+  return false;
+}
+
 template <int N>
 static bool inv_density_tma(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L,
                             float *dens, int *err, cudaStream_t s) {
@@ -617,9 +720,12 @@ template <typename T, int N> static void set_attrs() {
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_DENSITY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if constexpr (sizeof(T) == 4 && tma_inv_size(N))
+  if constexpr (sizeof(T) == 4 && tma_inv_size(N)) {
     cudaFuncSetAttribute(k_plane_inv_density_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tma_inv_smem<N>());
+    cudaFuncSetAttribute(k_zcol_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(tma_z_rows(N) * N * N * sizeof(float2)));
+  }
 }
 
 template <typename T> struct FastOps {
@@ -744,7 +850,20 @@ template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdAr
   count_launch(1);
 }
 
-template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s) {
+template <typename T>
+void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s, int *tma_err) {
+  if constexpr (sizeof(T) == 4) {
+    if (tma_err) {
+      bool done = false;
+#define SBSE_CALL(n) done = zcol_tma<n>(g, d, n_items, mult, tma_err, s)
+      SBSE_FAST_SWITCH(g.N, SBSE_CALL)
+#undef SBSE_CALL
+      if (done) {
+        count_launch(1);
+        return;
+      }
+    }
+  }
 #define SBSE_CALL(n) FastOps<T>::template z<n>(g, d, n_items, mult, s)
   SBSE_FAST_SWITCH(g.N, SBSE_CALL)
 #undef SBSE_CALL
@@ -792,7 +911,7 @@ void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, con
   template bool fast_supported<T>(int);                                                            \
   template void init_fast_kernels<T>();                                                            \
   template void launch_plane_fwd<T>(const GridTables<T> &, const XfwdArgs<T> &, cudaStream_t);     \
-  template void launch_zcol<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t);            \
+  template void launch_zcol<T>(const GridTables<T> &, C2<T> *, int, int, cudaStream_t, int *);     \
   template void launch_plane_inv_orb<T>(const GridTables<T> &, C2<T> *, int, const C2<T> *, int,   \
                                         T *, cudaStream_t, int *);                                 \
   template void launch_plane_inv_poisson<T>(const GridTables<T> &, C2<T> *, int, const PoissonOut &, \

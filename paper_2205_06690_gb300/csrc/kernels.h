@@ -51,7 +51,9 @@ template <typename T> struct XfwdArgs {
 
 template <typename T> void launch_xfwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
 template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
-template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s);
+// tma_err != null (FP32, N in 32 / 40 / 48 / 64): the bulk-copy streamed column kernel
+template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s,
+                                       int *tma_err = nullptr);
 // tma_err != null (FP32, density epilogue, N in 32 / 40 / 48 / 64): the bulk-copy streamed kernel,
 // which sets *tma_err if one of its bounded waits runs out
 template <typename T> void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items,

@@ -310,7 +310,7 @@ void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T
   if (fast_supported<T>(g.N)) {
     if (parts & RT_FWD_Z) {
       launch_plane_fwd<T>(g, fa, st);
-      launch_zcol<T>(g, data, n_items, Z_KINETIC, st);
+      launch_zcol<T>(g, data, n_items, Z_KINETIC, st, ctx->tma_planes ? ctx->flag : nullptr);
     }
     if (parts & RT_INV)
       launch_plane_inv_orb<T>(g, data, n_items, a_next, L, dens, st, ctx->tma_planes ? ctx->flag : nullptr);
@@ -334,7 +334,7 @@ void round_trip_poisson(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T>
   const int S = fa.n_items;
   if (fast_supported<T>(g.N)) {
     launch_plane_fwd<T>(g, fa, st);
-    launch_zcol<T>(g, pw, S, Z_POISSON, st);
+    launch_zcol<T>(g, pw, S, Z_POISSON, st);  // few items: the plain column kernel has more blocks
     launch_plane_inv_poisson<T>(g, pw, S, po, u_out, acc, em1_out, st);
   } else {
     launch_xfwd<T>(g, fa, st);
