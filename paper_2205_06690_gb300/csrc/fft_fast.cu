@@ -108,7 +108,9 @@ __device__ __forceinline__ void fwd_planes(const GView<T> &g, const XfwdArgs<T> 
     // of UB points issues all its loads before the first shared-memory store
     constexpr int UB = 8;
     auto run = [&](auto f) {
-#pragma unroll
+      // the batch loop is not unrolled: five variants of fully unrolled point loops overflowed the
+      // instruction cache (no-instruction stalls)
+#pragma unroll 1
       for (int k0 = 0; k0 < N; k0 += UB) {
         C v[UB];
 #pragma unroll

@@ -121,14 +121,13 @@ template <typename T> void launch_kick(const GridTables<T> &g, const double *q, 
                                        int L, double alpha, C2<T> *d, cudaStream_t s);
 template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const T *u,
                                              int P, int L, T tau, int feedback, cudaStream_t s);
-template <typename T> void launch_density(const GridTables<T> &g, const C2<T> *a, const C2<T> *d,
-                                          int P, int L, T *dens, cudaStream_t s);
 // cleaning of Eq. (15): overlaps O[c][s] = dV sum_r phi_s d_c (c < P*L complex columns)
-// use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait
+// use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait;
+// dens != null: the renormalisation also writes the induced density of each pair (Eq. 11)
 template <typename T> void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
                                         const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
                                         double dV, double *work, size_t work_bytes, bool use_tc,
-                                        int *err, cudaStream_t s);
+                                        int *err, cudaStream_t s, T *dens = nullptr);
 template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L);
 // d64 -> T conversion and FP64 -> T copies
 template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s);

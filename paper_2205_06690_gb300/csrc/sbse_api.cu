@@ -534,8 +534,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       if (pending) launch_half_phase<T>(g, acur, d, u, P, L, (T)(0.5 * p->dt), p->feedback, st);
       pending = false;
       launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
-                      ctx->tensor_cores != 0, ctx->flag, st);
-      launch_density<T>(g, acur, d, P, L, dn, st);
+                      ctx->tensor_cores != 0, ctx->flag, st, dn);
       CHECK_LAUNCH("clean");
       if ((rc = poisson<T>(ctx, g, dn, P, pw, u, accT, wts[n], em1, 0.5 * p->dt))) return rc;
       clk_end(ctx, ck);

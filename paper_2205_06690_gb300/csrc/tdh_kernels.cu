@@ -426,28 +426,6 @@ void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const T *u, i
   count_launch(1);
 }
 
-template <typename T>
-__global__ void k_density(long long ng, const C2<T> *a, const C2<T> *d, int P, int L, T *dens) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int pair = blockIdx.y;
-  if (r >= ng) return;
-  T acc = T(0);
-  for (int ell = 0; ell < L; ++ell) {
-    const C2<T> a0 = a[(long long)ell * ng + r];
-    const C2<T> dv = d[((long long)pair * L + ell) * ng + r];
-    acc += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
-  }
-  dens[(long long)pair * ng + r] = acc;
-}
-
-template <typename T>
-void launch_density(const GridTables<T> &g, const C2<T> *a, const C2<T> *d, int P, int L, T *dens,
-                    cudaStream_t s) {
-  dim3 grid((unsigned)((g.ng + 255) / 256), P);
-  k_density<T><<<grid, 256, 0, s>>>(g.ng, a, d, P, L, dens);
-  count_launch(1);
-}
-
 // ------------------------------------------------------------------------------------------
 // cleaning, Eq. (15): d_c <- d_c - sum_{s < N_occ} phi_s <phi_s|d_c>, then renormalisation of
 // eta^alpha = eta0 + d to its initial norm N0: d <- c d + (c - 1) eta0, c = (1 + x)^-1/2,
@@ -476,6 +454,32 @@ __global__ void k_renorm(long long ng, C2<T> *d, const C2<T> *a, int n_cols, int
   dv.x = (T(1) + cm1) * dv.x + cm1 * a0.x;
   dv.y = (T(1) + cm1) * dv.y + cm1 * a0.y;
   *dp = dv;
+}
+
+// renormalisation fused with the induced density of the cleaned orbitals (Eq. 11): block = 256
+// points of one pair; c - 1 of the pair's L columns is converted to T once per block (a per-point
+// FP64 -> FP32 conversion would load the narrow FP64 pipe)
+template <typename T>
+__global__ void k_renorm_density(long long ng, C2<T> *d, const C2<T> *a, int L, const double *cm1v, T *dens) {
+  extern __shared__ unsigned char sm_raw[];
+  T *cm1s = reinterpret_cast<T *>(sm_raw);
+  const int pair = blockIdx.y;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) cm1s[l] = (T)cm1v[(long long)pair * L + l];
+  __syncthreads();
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ng) return;
+  T acc = T(0);
+  for (int ell = 0; ell < L; ++ell) {
+    const T cm1 = cm1s[ell];
+    const C2<T> a0 = a[(long long)ell * ng + r];
+    C2<T> *dp = d + ((long long)pair * L + ell) * ng + r;
+    C2<T> dv = *dp;
+    dv.x = (T(1) + cm1) * dv.x + cm1 * a0.x;
+    dv.y = (T(1) + cm1) * dv.y + cm1 * a0.y;
+    *dp = dv;
+    acc += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+  }
+  dens[(long long)pair * ng + r] = acc;
 }
 
 // Overlaps of the complex columns d_c with the occupied orbitals, split over chunks of grid
@@ -661,7 +665,7 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
 template <typename T>
 void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
                   int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
-                  bool use_tc, int *err, cudaStream_t s) {
+                  bool use_tc, int *err, cudaStream_t s, T *dens) {
   (void)work_bytes;
   const int n_cols = P * L;
   const long long kc = gemm_kchunk(g.ng);
@@ -692,8 +696,13 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
     launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
   }
   k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
-  dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
-  k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);
+  if (dens) {
+    dim3 g3((unsigned)((g.ng + 255) / 256), P);
+    k_renorm_density<T><<<g3, 256, (size_t)L * sizeof(T), s>>>(g.ng, d, a, L, cm1, dens);
+  } else {
+    dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
+    k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);
+  }
   count_launch(3);
 }
 
@@ -781,11 +790,9 @@ void init_fft_kernels() {
                                double, C2<T> *, cudaStream_t);                                     \
   template void launch_half_phase<T>(const GridTables<T> &, C2<T> *, C2<T> *, const T *, int, int, \
                                      T, int, cudaStream_t);                                        \
-  template void launch_density<T>(const GridTables<T> &, const C2<T> *, const C2<T> *, int, int,   \
-                                  T *, cudaStream_t);                                              \
   template void launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *, C2<T> *,     \
                                 int, int, const double *, double, double *, size_t, bool, int *,   \
-                                cudaStream_t);                                                     \
+                                cudaStream_t, T *);                                                     \
   template size_t clean_work_bytes<T>(long long, int, int, int);                                   \
   template void launch_convert<T>(const double *, T *, long long, cudaStream_t);
 

@@ -105,7 +105,75 @@ __device__ __forceinline__ void split8(const float *x, uint4 *hi, uint4 *lo) {
 enum UmmaAMode { UA_PRODUCT = 0, UA_COMPLEX = 1 };
 
 // Producer: fill one stage. A unit = 8 rows x 32 points (4 core matrices along K); lane l covers
-// row (l & 7) of the group and core matrix kq = l >> 3, i.e. 8 consecutive points of one row.
+// row (l & 7) of the group and core matrix kq = l >> 3, i.e. 8 consecutive points of one row. Each
+// warp loads kUB units before converting and storing any of them, so that several global loads per
+// lane are in flight.
+constexpr int kUB = 4;
+
+template <int AMODE>
+__device__ __forceinline__ void load_unit(int u, int units_a, const float *F, const int2 *xi, int M, int m0,
+                                          const float *Y, int Nn, int n0, long long ng, long long k0,
+                                          long long kend, bool vec_ok, float *x) {
+  const int lane = threadIdx.x & 31;
+  const int rr = lane & 7, kq = lane >> 3;
+  const bool isA = u < units_a;
+  const int uu = isA ? u : u - units_a;
+  const int row = (uu >> 1) * 8 + rr;
+  const int kc = (uu & 1) * 4 + kq;  // core matrix index along K (0..7)
+  const long long kb = k0 + kc * 8;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 0.f;
+  const bool full = vec_ok && kb + 8 <= kend;
+  if (isA && AMODE == UA_COMPLEX) {
+    const int m = m0 + row;
+    if (m < M) {
+      const float *f = F + 2 * ((long long)(m >> 1) * ng + kb) + (m & 1);
+      if (full) {
+        const float4 c0 = *reinterpret_cast<const float4 *>(f - (m & 1));
+        const float4 c1 = *reinterpret_cast<const float4 *>(f - (m & 1) + 4);
+        const float4 c2 = *reinterpret_cast<const float4 *>(f - (m & 1) + 8);
+        const float4 c3 = *reinterpret_cast<const float4 *>(f - (m & 1) + 12);
+        if (m & 1) {
+          x[0] = c0.y; x[1] = c0.w; x[2] = c1.y; x[3] = c1.w; x[4] = c2.y; x[5] = c2.w; x[6] = c3.y; x[7] = c3.w;
+        } else {
+          x[0] = c0.x; x[1] = c0.z; x[2] = c1.x; x[3] = c1.z; x[4] = c2.x; x[5] = c2.z; x[6] = c3.x; x[7] = c3.z;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? f[2 * j] : 0.f;
+      }
+    }
+  } else if (isA) {
+    const int m = m0 + row;
+    if (m < M) {
+      const int2 q = xi[m];
+      const float *f1 = F + (long long)q.x * ng + kb, *f2 = F + (long long)q.y * ng + kb;
+      if (full) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(f1), a1 = *reinterpret_cast<const float4 *>(f1 + 4);
+        const float4 b0 = *reinterpret_cast<const float4 *>(f2), b1 = *reinterpret_cast<const float4 *>(f2 + 4);
+        x[0] = a0.x * b0.x; x[1] = a0.y * b0.y; x[2] = a0.z * b0.z; x[3] = a0.w * b0.w;
+        x[4] = a1.x * b1.x; x[5] = a1.y * b1.y; x[6] = a1.z * b1.z; x[7] = a1.w * b1.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? f1[j] * f2[j] : 0.f;
+      }
+    }
+  } else {
+    const int n = n0 + row;
+    if (n < Nn) {
+      const float *y = Y + (long long)n * ng + kb;
+      if (full) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(y), a1 = *reinterpret_cast<const float4 *>(y + 4);
+        x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+        x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? y[j] : 0.f;
+      }
+    }
+  }
+}
+
 template <int AMODE>
 __device__ __forceinline__ void produce_stage(uint8_t *st, int nt, const float *F, const int2 *xi, int M,
                                               int m0, const float *Y, int Nn, int n0, long long ng,
@@ -116,71 +184,29 @@ __device__ __forceinline__ void produce_stage(uint8_t *st, int nt, const float *
   uint8_t *b_lo = b_hi + nt * kUmBK * 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rr = lane & 7, kq = lane >> 3;
-  const int units_a = (kUmM / 8) * 2, units_b = (nt / 8) * 2;
+  const int units_a = (kUmM / 8) * 2, units_b = (nt / 8) * 2, total = units_a + units_b;
   const bool vec_ok = (ng & 3) == 0;  // 16-byte aligned rows
-  for (int u = warp; u < units_a + units_b; u += kUmThreads / 32) {
-    const bool isA = u < units_a;
-    const int uu = isA ? u : u - units_a;
-    const int row = (uu >> 1) * 8 + rr;
-    const int kc = (uu & 1) * 4 + kq;  // core matrix index along K (0..7)
-    const long long kb = k0 + kc * 8;
-    float x[8];
+  constexpr int W = kUmThreads / 32;
+  for (int u0 = warp; u0 < total; u0 += W * kUB) {
+    float x[kUB][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = 0.f;
-    const bool full = vec_ok && kb + 8 <= kend;
-    if (isA && AMODE == UA_COMPLEX) {
-      const int m = m0 + row;
-      if (m < M) {
-        const float *f = F + 2 * ((long long)(m >> 1) * ng + kb) + (m & 1);
-        if (full) {
-          const float4 c0 = *reinterpret_cast<const float4 *>(f - (m & 1));
-          const float4 c1 = *reinterpret_cast<const float4 *>(f - (m & 1) + 4);
-          const float4 c2 = *reinterpret_cast<const float4 *>(f - (m & 1) + 8);
-          const float4 c3 = *reinterpret_cast<const float4 *>(f - (m & 1) + 12);
-          if (m & 1) {
-            x[0] = c0.y; x[1] = c0.w; x[2] = c1.y; x[3] = c1.w; x[4] = c2.y; x[5] = c2.w; x[6] = c3.y; x[7] = c3.w;
-          } else {
-            x[0] = c0.x; x[1] = c0.z; x[2] = c1.x; x[3] = c1.z; x[4] = c2.x; x[5] = c2.z; x[6] = c3.x; x[7] = c3.z;
-          }
-        } else {
+    for (int i = 0; i < kUB; ++i)
+      if (u0 + i * W < total)
+        load_unit<AMODE>(u0 + i * W, units_a, F, xi, M, m0, Y, Nn, n0, ng, k0, kend, vec_ok, x[i]);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? f[2 * j] : 0.f;
-        }
-      }
-    } else if (isA) {
-      const int m = m0 + row;
-      if (m < M) {
-        const int2 q = xi[m];
-        const float *f1 = F + (long long)q.x * ng + kb, *f2 = F + (long long)q.y * ng + kb;
-        if (full) {
-          const float4 a0 = *reinterpret_cast<const float4 *>(f1), a1 = *reinterpret_cast<const float4 *>(f1 + 4);
-          const float4 b0 = *reinterpret_cast<const float4 *>(f2), b1 = *reinterpret_cast<const float4 *>(f2 + 4);
-          x[0] = a0.x * b0.x; x[1] = a0.y * b0.y; x[2] = a0.z * b0.z; x[3] = a0.w * b0.w;
-          x[4] = a1.x * b1.x; x[5] = a1.y * b1.y; x[6] = a1.z * b1.z; x[7] = a1.w * b1.w;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? f1[j] * f2[j] : 0.f;
-        }
-      }
-    } else {
-      const int n = n0 + row;
-      if (n < Nn) {
-        const float *y = Y + (long long)n * ng + kb;
-        if (full) {
-          const float4 a0 = *reinterpret_cast<const float4 *>(y), a1 = *reinterpret_cast<const float4 *>(y + 4);
-          x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
-          x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) x[j] = (kb + j < kend) ? y[j] : 0.f;
-        }
-      }
+    for (int i = 0; i < kUB; ++i) {
+      const int u = u0 + i * W;
+      if (u >= total) break;
+      const bool isA = u < units_a;
+      const int uu = isA ? u : u - units_a;
+      const int row = (uu >> 1) * 8 + rr;
+      const int kc = (uu & 1) * 4 + kq;
+      uint4 hi, lo;
+      split8(x[i], &hi, &lo);
+      const uint32_t off = canon_off(row, kc);
+      *reinterpret_cast<uint4 *>((isA ? a_hi : b_hi) + off) = hi;
+      *reinterpret_cast<uint4 *>((isA ? a_lo : b_lo) + off) = lo;
     }
-    uint4 hi, lo;
-    split8(x, &hi, &lo);
-    const uint32_t off = canon_off(row, kc);
-    *reinterpret_cast<uint4 *>((isA ? a_hi : b_hi) + off) = hi;
-    *reinterpret_cast<uint4 *>((isA ? a_lo : b_lo) + off) = lo;
   }
 }
 
@@ -410,35 +436,52 @@ __global__ void __launch_bounds__(kUmThreads)
       for (int j = 0; j < 16; ++j) row[j] = __uint_as_float(rr[j]);
     }
     __syncthreads();
-    for (int cl = warp; cl < kUmM / 2; cl += kUmThreads / 32) {
-      const int c = c0 + cl;
-      if (c >= n_cols) continue;
-      float2 *dc = reinterpret_cast<float2 *>(d) + (long long)c * ng;
-      const float2 *ac = reinterpret_cast<const float2 *>(a) + (long long)(c % L) * ng;
-      // FP32 sums over the 128 points of the half (the FP64 pipe of this GPU is too slow for
-      // per-point work); they are carried on in FP64 per tile and across tiles
-      float v1 = 0.f, v2 = 0.f;
+    // each warp updates CB complex columns at a time, with all their loads issued together
+    constexpr int CB = 4, PP = kHalf / 32;
+    for (int cb = warp * CB; cb < kUmM / 2; cb += CB * (kUmThreads / 32)) {
+      float2 dv[CB][PP], av[CB][PP];
 #pragma unroll
-      for (int p = lane; p < kHalf; p += 32) {
-        const long long r = r0 + half * kHalf + p;
-        if (r < ng) {
-          float2 dv = dc[r];
-          dv.x -= Dsm[(2 * cl) * kLd + p];
-          dv.y -= Dsm[(2 * cl + 1) * kLd + p];
-          dc[r] = dv;
-          const float2 a0 = ac[r];
-          v1 += 2.f * (a0.x * dv.x + a0.y * dv.y);
-          v2 += dv.x * dv.x + dv.y * dv.y;
+      for (int i = 0; i < CB; ++i) {
+        const int c = c0 + cb + i;
+        const float2 *dc = reinterpret_cast<const float2 *>(d) + (long long)c * ng;
+        const float2 *ac = reinterpret_cast<const float2 *>(a) + (long long)(c % L) * ng;
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+          const long long r = r0 + half * kHalf + lane + 32 * j;
+          const bool in = c < n_cols && r < ng;
+          dv[i][j] = in ? dc[r] : make_float2(0.f, 0.f);
+          av[i][j] = in ? ac[r] : make_float2(0.f, 0.f);
         }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-      }
-      if (lane == 0) {
-        colsum[cl][0] += (double)v1;
-        colsum[cl][1] += (double)v2;
+      for (int i = 0; i < CB; ++i) {
+        const int cl = cb + i, c = c0 + cl;
+        float2 *dc = reinterpret_cast<float2 *>(d) + (long long)c * ng;
+        // FP32 sums over the 128 points of the half (the FP64 pipe of this GPU is too slow for
+        // per-point work); they are carried on in FP64 per tile and across tiles
+        float v1 = 0.f, v2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+          const int p = lane + 32 * j;
+          const long long r = r0 + half * kHalf + p;
+          if (c < n_cols && r < ng) {
+            float2 x = dv[i][j];
+            x.x -= Dsm[(2 * cl) * kLd + p];
+            x.y -= Dsm[(2 * cl + 1) * kLd + p];
+            dc[r] = x;
+            v1 += 2.f * (av[i][j].x * x.x + av[i][j].y * x.y);
+            v2 += x.x * x.x + x.y * x.y;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+          v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+        }
+        if (lane == 0) {
+          colsum[cl][0] += (double)v1;
+          colsum[cl][1] += (double)v2;
+        }
       }
     }
   }
