@@ -119,8 +119,10 @@ void launch_reduce_cols(const double *part, int rows, int cols, double scale, do
                         cudaStream_t s);
 template <typename T> void launch_kick(const GridTables<T> &g, const double *q, int P, const C2<T> *a,
                                        int L, double alpha, C2<T> *d, cudaStream_t s);
-template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const T *u,
-                                             int P, int L, T tau, int feedback, cudaStream_t s);
+// pending half potential step before a cleaning: P = exp(-i V_loc dt/2) from the grid tables, E - 1
+// per pair (tau = dt/2) from em1 (null: no feedback)
+template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const C2<T> *em1,
+                                             int P, int L, cudaStream_t s);
 // cleaning of Eq. (15): overlaps O[c][s] = dV sum_r phi_s d_c (c < P*L complex columns)
 // use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait;
 // dens != null: the renormalisation also writes the induced density of each pair (Eq. 11)

@@ -395,7 +395,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   }
   void *vp;
   C *a0, *a1, *d, *pw;
-  T *u, *dn;
+  T *dn;
   double *wacc, *n0, *part, *cwork, *coef;
   int4 *prod;
   if ((rc = ensure(ctx, WS_A0, (size_t)L * ng * sizeof(C), &vp))) return rc;
@@ -404,8 +404,6 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   a1 = (C *)vp;
   if ((rc = ensure(ctx, WS_D, (size_t)P * L * ng * sizeof(C), &vp))) return rc;
   d = (C *)vp;
-  if ((rc = ensure(ctx, WS_U, (size_t)P * ng * sizeof(T), &vp))) return rc;
-  u = (T *)vp;
   if ((rc = ensure(ctx, WS_DN, (size_t)P * ng * sizeof(T), &vp))) return rc;
   dn = (T *)vp;
   const size_t pw_bytes = std::max((size_t)S * ng * sizeof(C), (size_t)S * ng * sizeof(C2<double>));
@@ -469,7 +467,6 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
                                      wacc)))
     return rc;
   launch_kick<T>(g, wacc, P, a0, L, p->alpha, d, st);
-  CK(cudaMemsetAsync(u, 0, (size_t)P * ng * sizeof(T), st));
   CHECK_LAUNCH("kick");
 
   // ---- time loop (Eq. 10 split-operator, Eq. 15 cleaning, Eq. 13 damped trapezoid)
@@ -531,12 +528,12 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     if (M > 0 && n % M == 0) {
       size_t ck = 0;
       clk_begin(ctx, 2, &ck);
-      if (pending) launch_half_phase<T>(g, acur, d, u, P, L, (T)(0.5 * p->dt), p->feedback, st);
+      if (pending) launch_half_phase<T>(g, acur, d, em1, P, L, st);
       pending = false;
       launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
                       ctx->tensor_cores != 0, ctx->flag, st, dn);
       CHECK_LAUNCH("clean");
-      if ((rc = poisson<T>(ctx, g, dn, P, pw, u, accT, wts[n], em1, 0.5 * p->dt))) return rc;
+      if ((rc = poisson<T>(ctx, g, dn, P, pw, nullptr, accT, wts[n], em1, 0.5 * p->dt))) return rc;
       clk_end(ctx, ck);
     }
     size_t c0 = 0;
@@ -593,9 +590,11 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   poisson_step:
     size_t c1 = 0;
     clk_begin(ctx, 1, &c1);
+    // before a cleaning the potential is recomputed from the cleaned orbitals (and accumulated
+    // then); this one only supplies E - 1 at dt/2 for the pending half step
     const bool recomputed = (M > 0 && (n + 1) % M == 0 && n + 1 < Nt);
-    if ((rc = poisson<T>(ctx, g, dn, P, pw, u, recomputed ? nullptr : accT,
-                         recomputed ? 0.0 : wts[n + 1], recomputed ? nullptr : em1, p->dt)))
+    if ((rc = poisson<T>(ctx, g, dn, P, pw, nullptr, recomputed ? nullptr : accT,
+                         recomputed ? 0.0 : wts[n + 1], em1, recomputed ? 0.5 * p->dt : p->dt)))
       return rc;
     if (sizeof(T) != sizeof(double) && ((n + 1) % kFlush == 0 || n + 1 == Nt))
       launch_flush_acc<T>(wacc, accT, (long long)P * ng, st);

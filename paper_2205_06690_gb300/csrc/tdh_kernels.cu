@@ -397,32 +397,31 @@ void launch_kick(const GridTables<T> &g, const double *q, int P, const C2<T> *a,
 // ------------------------------------------------------------------------------------------
 // pending half potential step on (eta0, d) before cleaning (same rule as the x-forward pass)
 
+// the pending half step of the potential before a cleaning, on the difference form:
+// d <- P [(E - 1) a + E d], a <- P a, with the tables P = exp(-i V_loc dt/2) and E - 1 of each pair
+// at tau = dt/2 (written by the preceding Poisson epilogue; null without feedback)
 template <typename T>
-__global__ void k_half_phase(GView<T> g, C2<T> *a, C2<T> *d, const T *u, int P, int L, T tau,
-                             int feedback) {
+__global__ void k_half_phase(long long ng, C2<T> *a, C2<T> *d, const C2<T> *pv, const C2<T> *em1, int P,
+                             int L) {
   using C = C2<T>;
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int ell = blockIdx.y;
-  if (r >= g.ng) return;
-  const C av = a[(long long)ell * g.ng + r];
-  const C pv = expmi<T>(g.v_loc[r] * tau);
+  if (r >= ng) return;
+  const C av = a[(long long)ell * ng + r];
+  const C p = pv[r];
   for (int pair = 0; pair < P; ++pair) {
-    const T uu = feedback ? u[(long long)pair * g.ng + r] : T(0);
-    T s, c;
-    sincos_t(T(0.5) * uu * tau, &s, &c);
-    const C em1 = C{T(-2) * s * s, T(-2) * s * c};
-    const C E = C{T(1) + em1.x, em1.y};
-    C *dp = d + ((long long)pair * L + ell) * g.ng + r;
-    *dp = cmul(pv, cadd(cmul(em1, av), cmul(E, *dp)));
+    const C em = em1 ? em1[(long long)pair * ng + r] : C{T(0), T(0)};
+    C *dp = d + ((long long)pair * L + ell) * ng + r;
+    *dp = pair_phase<T>(p, em, av, *dp);
   }
-  a[(long long)ell * g.ng + r] = cmul(pv, av);
+  a[(long long)ell * ng + r] = cmul(p, av);
 }
 
 template <typename T>
-void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const T *u, int P, int L, T tau,
-                       int feedback, cudaStream_t s) {
+void launch_half_phase(const GridTables<T> &g, C2<T> *a, C2<T> *d, const C2<T> *em1, int P, int L,
+                       cudaStream_t s) {
   dim3 grid((unsigned)((g.ng + 255) / 256), L);
-  k_half_phase<T><<<grid, 256, 0, s>>>(view(g), a, d, u, P, L, tau, feedback);
+  k_half_phase<T><<<grid, 256, 0, s>>>(g.ng, a, d, g.pv_half, em1, P, L);
   count_launch(1);
 }
 
@@ -788,8 +787,8 @@ void init_fft_kernels() {
                                  C2<T> *, double *, int *, cudaStream_t);                          \
   template void launch_kick<T>(const GridTables<T> &, const double *, int, const C2<T> *, int,     \
                                double, C2<T> *, cudaStream_t);                                     \
-  template void launch_half_phase<T>(const GridTables<T> &, C2<T> *, C2<T> *, const T *, int, int, \
-                                     T, int, cudaStream_t);                                        \
+  template void launch_half_phase<T>(const GridTables<T> &, C2<T> *, C2<T> *, const C2<T> *, int, int, \
+                                     cudaStream_t);                                              \
   template void launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *, C2<T> *,     \
                                 int, int, const double *, double, double *, size_t, bool, int *,   \
                                 cudaStream_t, T *);                                                     \
