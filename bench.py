@@ -16,6 +16,7 @@ Under torchrun every rank runs its own replica of the workload with its own stoc
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -164,6 +165,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ["fft_fast.cu", "fft_reg.cuh", "passes.cuh", "tma.cuh", "common.cuh", "kernels.h"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2205_06690_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(phase, workload, mixed):
+    """DRAM bytes (read + write) per launch of the pass, from the committed ncu summary, when it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"pair_passes_{workload}_traffic.txt")
+    if phase is None or not mixed or not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_sha256_16") != kernel_source_hash():
+        return None, "kernel sources changed since the ncu capture"
+    v = d.get("dram_bytes_per_launch", {}).get(str(phase))
+    return (float(v), os.path.relpath(path, ROOT)) if v else (None, None)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -282,7 +308,7 @@ def main():
     clocks = clk.stop()
     launches = B.sbse_kernel_launches() - launches0
     ms = e0.elapsed_time(e1)
-    phase = {ph: B.sbse_phase_time(ctx.h, ph) for ph in range(5)}
+    phase = {ph: B.sbse_phase_time(ctx.h, ph) for ph in range(8)}
     B.sbse_profile(ctx.h, False)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -368,14 +394,40 @@ def main():
     h2d = system.v_loc.nbytes + phi.nbytes + eps.nbytes + pre.n_s * pre.n_occ * 8
     d2h = pre.n_exc * 8
 
-    # roofline of the dominant kernel group: one propagation step of all P*L + L orbitals
-    # (x pass with the potential phase, y, z with the kinetic phase, y, x with the density)
+    # Roofline. Algorithmic unit: one read and one write of every complex value of the pair batch
+    # (P L n_g points, 16 B/point in FP32). Each of the three passes of a step (phases 5, 6, 7,
+    # timed by events on the library's stream inside the timed region) is one such sweep; the
+    # dominant kernel is the pass with the largest share. The whole step (phase 0) is reported
+    # against the same per-step figure, so its fraction shows the cost of three sweeps per step.
     peak, src = measured_peaks()
     csize = 8 if prec == B.SBSE_MIXED else 16
-    alg_bytes = (P * pre.n_s + pre.n_s) * pre.N ** 3 * 2 * csize
+    sweep_bytes = P * pre.n_s * pre.N ** 3 * 2 * csize
+    pass_names = {5: "forward plane pass k_plane_fwd (potential phase + x, y FFTs)",
+                  6: "z-column pass k_zcol_tma (z FFT, kinetic phase, inverse z FFT)",
+                  7: "inverse plane pass k_plane_inv_density_tma (y, x inverse FFTs + density)"}
+    passes = {}
+    for ph, name in pass_names.items():
+        t, nl = phase[ph]
+        if nl:
+            gbs = sweep_bytes / (t / nl / 1e3) / 1e9
+            passes[str(ph)] = {"kernel": name, "avg_us": 1e3 * t / nl, "launches": nl,
+                               "achieved": gbs, "frac": gbs / peak, "share_of_step": t / ms}
+    dom = max(passes, key=lambda k: passes[k]["share_of_step"]) if passes else None
+    traffic, traffic_note = profiled_traffic(dom and int(dom), pre.name, prec == B.SBSE_MIXED)
     ms0, n0 = phase[0]
-    achieved = alg_bytes / (ms0 / n0 / 1e3) / 1e9 if n0 else None
-    dominant_share = ms0 / ms if ms else None
+    step_gbs = (sweep_bytes + pre.n_s * pre.N ** 3 * 2 * csize) / (ms0 / n0 / 1e3) / 1e9 if n0 else None
+    if dom:
+        roofline = {"bound": "hbm", "achieved": passes[dom]["achieved"], "peak": peak, "unit": "GB/s",
+                    "frac": passes[dom]["frac"], "traffic": traffic, "traffic_source": traffic_note,
+                    "kernel": passes[dom]["kernel"], "bytes_per_launch": sweep_bytes,
+                    "avg_launch_us": passes[dom]["avg_us"], "share_of_step": passes[dom]["share_of_step"],
+                    "peak_source": src, "passes": passes,
+                    "step": {"achieved": step_gbs, "frac": step_gbs / peak if step_gbs else None,
+                             "share_of_step": ms0 / ms if ms else None}}
+    else:
+        roofline = {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                    "frac": step_gbs / peak if step_gbs else None, "traffic": None,
+                    "kernel": "propagation step", "peak_source": src}
     line = {
         "metric": "W-rho applications/sec (stochastic TDH, all pairs) + A build",
         "value": value, "unit": "W-applications/s", "n_gpus": world, "steps": args.steps,
@@ -392,10 +444,7 @@ def main():
         "e2e": {"value": world * P / e2e_s, "unit": "W-applications/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": "propagation step (3 FFT-pass kernels over all orbitals)",
-                     "peak_source": src, "share_of_step": dominant_share},
+        "roofline": roofline,
         "a_build_ms": a_build_ms,
         "phase_ms_per_step": {str(k): v[0] / args.steps for k, v in phase.items()},
         "excitons_ha": [float(x) for x in ev],

@@ -212,7 +212,10 @@ int sbse_kernel_launches(long long *count);
  * number of launches of one phase since the last reset (enable resets the counters).
  * phase: 0 = orbital propagation step (phase + 3D FFT + kinetic + inverse FFT + induced density),
  *        1 = Poisson solve and time-integral accumulation, 2 = cleaning, 3 = contractions (K, D),
- *        4 = A assembly + eigensolve. Errors: INVALID_ARG, CUDA. */
+ *        4 = A assembly + eigensolve; inside phase 0, the three passes over the pair batch on
+ *        grids with the register-pencil FFT: 5 = forward plane pass (potential phase + x, y FFTs),
+ *        6 = z-column pass (z FFT, kinetic phase, inverse z FFT), 7 = inverse plane pass (+ density).
+ *        Errors: INVALID_ARG, CUDA. */
 int sbse_profile(sbse_ctx *ctx, int enable);
 int sbse_phase_time(sbse_ctx *ctx, int phase, double *ms, long long *launches);
 

@@ -126,10 +126,12 @@ template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C
 // cleaning of Eq. (15): overlaps O[c][s] = dV sum_r phi_s d_c (c < P*L complex columns)
 // use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait;
 // dens != null: the renormalisation also writes the induced density of each pair (Eq. 11)
+// phi_can != null (FP32 only): the projection update on the tensor cores from pre-split orbitals
 template <typename T> void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
                                         const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
                                         double dV, double *work, size_t work_bytes, bool use_tc,
-                                        int *err, cudaStream_t s, T *dens = nullptr);
+                                        const uint8_t *phi_can, int *err, cudaStream_t s,
+                                        T *dens = nullptr);
 template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L);
 // d64 -> T conversion and FP64 -> T copies
 template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s);
@@ -155,11 +157,16 @@ int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const floa
                               cudaStream_t s);
 
 // cleaning update on the tensor cores: d_c -= sum_s O[2c+h][s] phi_s (h = re / im parts), plus
-// per-tile norm partials npart[tile][c][2] (tiles of umma_clean_update_tiles(ng) rows)
-void launch_umma_clean_update(const double *ov, int n_cols, const float *phi, int n_occ, long long ng,
-                              float *d_interleaved, const float *a_interleaved, int L, double *npart, int *err,
-                              cudaStream_t s);
+// per-tile norm partials npart[tile][c][2] (tiles of umma_clean_update_tiles(ng) rows). phi_can holds
+// the occupied orbitals as pre-split canonical operand tiles (umma_prepare_update_phi, once per
+// propagation); o_can is scratch of umma_update_o_bytes for the overlaps' tiles.
+void launch_umma_clean_update(const double *ov, int n_cols, const uint8_t *phi_can, int n_occ, long long ng,
+                              float *d_interleaved, const float *a_interleaved, int L, double *npart,
+                              uint8_t *o_can, int *err, cudaStream_t s);
 long long umma_clean_update_tiles(long long ng);
+size_t umma_update_phi_bytes(long long ng, int n_occ);
+size_t umma_update_o_bytes(int n_cols, int n_occ);
+void umma_prepare_update_phi(const float *phi, int n_occ, long long ng, uint8_t *phi_can, cudaStream_t s);
 
 // ---- eigensolver (eig.cu)
 int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, cudaStream_t s);

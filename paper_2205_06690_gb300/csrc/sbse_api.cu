@@ -89,7 +89,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -307,13 +307,23 @@ void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T
                          int n_items, const C2<T> *a_next, int L, T *dens, cudaStream_t st = nullptr,
                          int parts = RT_ALL) {
   if (!st) st = ctx->stream;
+  // the pair batch (dens != null) times each pass separately when profiling (phases 5, 6, 7)
+  const bool sub = dens != nullptr && st == ctx->stream;
+  size_t ck = 0;
   if (fast_supported<T>(g.N)) {
     if (parts & RT_FWD_Z) {
+      if (sub) clk_begin(ctx, 5, &ck);
       launch_plane_fwd<T>(g, fa, st);
+      if (sub) clk_end(ctx, ck);
+      if (sub) clk_begin(ctx, 6, &ck);
       launch_zcol<T>(g, data, n_items, Z_KINETIC, st, ctx->tma_planes ? ctx->flag : nullptr);
+      if (sub) clk_end(ctx, ck);
     }
-    if (parts & RT_INV)
+    if (parts & RT_INV) {
+      if (sub) clk_begin(ctx, 7, &ck);
       launch_plane_inv_orb<T>(g, data, n_items, a_next, L, dens, st, ctx->tma_planes ? ctx->flag : nullptr);
+      if (sub) clk_end(ctx, ck);
+    }
   } else {
     if (parts & RT_FWD_Z) {
       launch_xfwd<T>(g, fa, st);
@@ -434,6 +444,13 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   const size_t cw = clean_work_bytes<T>(ng, ctx->n_occ, P, L);
   if ((rc = ensure(ctx, WS_CLEAN, cw, &vp))) return rc;
   cwork = (double *)vp;
+  // tensor-core cleaning update (FP32): the occupied orbitals as pre-split operand tiles
+  const uint8_t *phi_can = nullptr;
+  if (sizeof(T) == sizeof(float) && ctx->tensor_cores) {
+    if ((rc = ensure(ctx, WS_PHICAN, umma_update_phi_bytes(ng, ctx->n_occ), &vp))) return rc;
+    umma_prepare_update_phi(ctx->phi32, ctx->n_occ, ng, (uint8_t *)vp, st);
+    phi_can = (const uint8_t *)vp;
+  }
   if ((rc = ensure(ctx, WS_COEF, coef_host.size() * sizeof(double), &vp))) return rc;
   coef = (double *)vp;
   if ((rc = ensure(ctx, WS_IDX, (size_t)S * sizeof(int4), &vp))) return rc;
@@ -531,7 +548,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       if (pending) launch_half_phase<T>(g, acur, d, em1, P, L, st);
       pending = false;
       launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
-                      ctx->tensor_cores != 0, ctx->flag, st, dn);
+                      ctx->tensor_cores != 0, phi_can, ctx->flag, st, dn);
       CHECK_LAUNCH("clean");
       if ((rc = poisson<T>(ctx, g, dn, P, pw, nullptr, accT, wts[n], em1, 0.5 * p->dt))) return rc;
       clk_end(ctx, ck);
@@ -1081,7 +1098,7 @@ int sbse_profile(sbse_ctx *ctx, int enable) {
 }
 
 int sbse_phase_time(sbse_ctx *ctx, int phase, double *ms, long long *launches) {
-  if (!ctx || !ms || !launches || phase < 0 || phase > 4) return SBSE_ERR_INVALID_ARG;
+  if (!ctx || !ms || !launches || phase < 0 || phase > 7) return SBSE_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
   double tot = 0.0;
   long long cnt = 0;

@@ -658,13 +658,15 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
   b += (size_t)(ptb * n_cols * 2) * sizeof(double);             // norm partials
   b += (size_t)(n_cols * 2) * sizeof(double);                   // norm sums
   b += (size_t)n_cols * sizeof(double);                         // c - 1 per column
+  b = (b + 127) / 128 * 128;
+  if (sizeof(T) == 4) b += umma_update_o_bytes((int)n_cols, n_occ);  // overlaps as operand tiles
   return b;
 }
 
 template <typename T>
 void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
                   int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
-                  bool use_tc, int *err, cudaStream_t s, T *dens) {
+                  bool use_tc, const uint8_t *phi_can, int *err, cudaStream_t s, T *dens) {
   (void)work_bytes;
   const int n_cols = P * L;
   const long long kc = gemm_kchunk(g.ng);
@@ -686,9 +688,12 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
     count_launch(1);
     launch_reduce_cols(part, (int)chunks, n_cols * n_occ * 2, dV, ov, s);
   }
-  if (use_tc && sizeof(T) == sizeof(float)) {
-    launch_umma_clean_update(ov, n_cols, reinterpret_cast<const float *>(phi_occ), n_occ, g.ng,
-                             reinterpret_cast<float *>(d), reinterpret_cast<const float *>(a), L, npart, err, s);
+  if (phi_can && sizeof(T) == sizeof(float)) {
+    size_t o_off = (size_t)((cm1 + n_cols) - work) * sizeof(double);
+    o_off = (o_off + 127) / 128 * 128;
+    uint8_t *o_can = reinterpret_cast<uint8_t *>(work) + o_off;
+    launch_umma_clean_update(ov, n_cols, phi_can, n_occ, g.ng, reinterpret_cast<float *>(d),
+                             reinterpret_cast<const float *>(a), L, npart, o_can, err, s);
     launch_reduce_cols(npart, (int)umma_clean_update_tiles(g.ng), n_cols * 2, dV, sums, s);
   } else {
     k_clean_update2<T><<<(unsigned)ptb, 256, 0, s>>>(g.ng, phi_occ, n_occ, ov, d, a, n_cols, L, npart);
@@ -790,8 +795,8 @@ void init_fft_kernels() {
   template void launch_half_phase<T>(const GridTables<T> &, C2<T> *, C2<T> *, const C2<T> *, int, int, \
                                      cudaStream_t);                                              \
   template void launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *, C2<T> *,     \
-                                int, int, const double *, double, double *, size_t, bool, int *,   \
-                                cudaStream_t, T *);                                                     \
+                                int, int, const double *, double, double *, size_t, bool,          \
+                                const uint8_t *, int *, cudaStream_t, T *);                                                     \
   template size_t clean_work_bytes<T>(long long, int, int, int);                                   \
   template void launch_convert<T>(const double *, T *, long long, cudaStream_t);
 

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace sbse {
 
@@ -315,17 +316,58 @@ __global__ void __launch_bounds__(kUmThreads)
 
 // ---- cleaning projection update on the tensor cores ------------------------------------------
 // d_c(r) -= sum_s O[c][s] phi_s(r) (Eq. 15) as D[m][r] = sum_s O[m][s] phi_s(r) with m = 2c + h the
-// real / imaginary row of column c; A = O (128 rows per tile), B = phi^T (256 grid points per tile,
-// transposed into the K-major layout by the producer), K = the occupied states in stages of 64.
-// The epilogue subtracts D from d in place (coalesced through shared memory) and writes per-tile
-// partial sums of 2 Re(conj(eta0) d) and |d|^2 per column for the renormalisation.
+// real / imaginary row of column c; A = O (128 rows per tile), B = phi^T (256 grid points per tile),
+// K = the occupied states in chunks of 64. Both operands are split into BF16 high / low parts and
+// laid out in the canonical K-major tiles once (B once per propagation, A once per cleaning), so a
+// CTA only issues two bulk copies (TMA) per K chunk and then the MMAs. The epilogue subtracts D
+// from d in place (coalesced through shared memory) and writes per-tile partial sums of
+// 2 Re(conj(eta0) d) and |d|^2 per column for the renormalisation.
 constexpr int kCuN = 256;
+constexpr unsigned kCanA = 2u * kUmM * kUmBK * 2;  // bytes of one A chunk (hi, lo)
+constexpr unsigned kCanB = 2u * kCuN * kUmBK * 2;  // bytes of one B chunk (hi, lo)
+
+// canonical BF16 hi / lo tiles: out[tile][chunk] = hi (R x 64) then lo (R x 64); element (row, k)
+// of a tile is src(tile R + row, chunk 64 + k), zero outside the source. Thread per (row, group of
+// 8 k); consecutive threads take consecutive rows.
+struct SrcRowsF64 {  // O[m][s], row-major FP64
+  const double *p;
+  long long rows;
+  int K;
+  __device__ float operator()(long long r, int k) const { return (r < rows && k < K) ? (float)p[r * K + k] : 0.f; }
+};
+struct SrcColsF32 {  // phi^T: element (r, s) = phi[s][r]
+  const float *p;
+  long long rows;
+  int K;
+  __device__ float operator()(long long r, int k) const { return (r < rows && k < K) ? p[(long long)k * rows + r] : 0.f; }
+};
+
+template <int R, class Src>
+__global__ void k_canon_tiles(Src src, long long n_tiles, int n_kc, uint8_t *out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per_chunk = (long long)R * 8, per_tile = per_chunk * n_kc;
+  if (t >= n_tiles * per_tile) return;
+  const long long tile = t / per_tile;
+  const long long rem = t - tile * per_tile;
+  const int kc = (int)(rem / per_chunk);
+  const int rem2 = (int)(rem - (long long)kc * per_chunk);
+  const int g = rem2 / R, row = rem2 - g * R;
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = src(tile * R + row, kc * kUmBK + g * 8 + j);
+  uint4 hi, lo;
+  split8(x, &hi, &lo);
+  uint8_t *base = out + (tile * n_kc + kc) * (2ll * R * kUmBK * 2);
+  const uint32_t off = canon_off(row, g);
+  *reinterpret_cast<uint4 *>(base + off) = hi;
+  *reinterpret_cast<uint4 *>(base + (size_t)R * kUmBK * 2 + off) = lo;
+}
 
 __global__ void __launch_bounds__(kUmThreads)
-    k_umma_clean_update(const double *ov, int M, const float *phi, int n_occ, long long ng, float *d,
+    k_umma_clean_update(const uint8_t *o_can, int M, const uint8_t *phi_can, int n_kc, long long ng, float *d,
                         const float *a, int L, double *npart, int *err) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar, tbar;
   __shared__ uint32_t tmem_slot;
   uint8_t *a_hi = smem, *a_lo = a_hi + kUmM * kUmBK * 2;
   uint8_t *b_hi = a_lo + kUmM * kUmBK * 2, *b_lo = b_hi + kCuN * kUmBK * 2;
@@ -340,57 +382,28 @@ __global__ void __launch_bounds__(kUmThreads)
   }
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
+    tma_bar_init(&tbar, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = make_idesc(kUmM, kCuN);
-  const int n_iter = (n_occ + kUmBK - 1) / kUmBK;
-  bool ok = true;
-  for (int it = 0; it < n_iter; ++it) {
-    const int s0 = it * kUmBK;
-    bool w = true;
-    if (it > 0) w = mbar_wait(smem_u32(&mbar), (uint32_t)((it - 1) & 1));
-    if (!__syncthreads_and(w)) {
+  bool ok = true, tma_pending = false;
+  int mma_issued = 0;
+  for (int it = 0; it < n_kc; ++it) {
+    // the previous chunk's MMAs have completed (waited below), so its operand tiles can be replaced
+    if (threadIdx.x == 0) {
+      tma_bar_expect(&tbar, kCanA + kCanB);
+      tma_load_1d(a_hi, o_can + ((size_t)blockIdx.y * n_kc + it) * kCanA, kCanA, &tbar);
+      tma_load_1d(b_hi, phi_can + ((size_t)blockIdx.x * n_kc + it) * kCanB, kCanB, &tbar);
+    }
+    tma_pending = true;
+    if (!__syncthreads_and(tma_bar_wait(&tbar, (unsigned)(it & 1)))) {
       ok = false;
       break;
     }
-    // A: O rows (FP64) -> BF16 hi / lo; unit = 8 rows x 32 states
-    for (int u = warp; u < (kUmM / 8) * 2; u += kUmThreads / 32) {
-      const int row = (u >> 1) * 8 + (lane & 7);
-      const int kc = (u & 1) * 4 + (lane >> 3);
-      const int m = m0 + row;
-      float x[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int sidx = s0 + kc * 8 + j;
-        x[j] = (m < M && sidx < n_occ) ? (float)ov[(long long)m * n_occ + sidx] : 0.f;
-      }
-      uint4 hi, lo;
-      split8(x, &hi, &lo);
-      *reinterpret_cast<uint4 *>(a_hi + canon_off(row, kc)) = hi;
-      *reinterpret_cast<uint4 *>(a_lo + canon_off(row, kc)) = lo;
-    }
-    // B: phi^T, row = grid point, k = state; unit = 32 points x 8 states, lane = point
-    for (int u = warp; u < (kCuN / 32) * (kUmBK / 8); u += kUmThreads / 32) {
-      const int row = (u % (kCuN / 32)) * 32 + lane;
-      const int kc = u / (kCuN / 32);
-      const long long r = r0 + row;
-      float x[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int sidx = s0 + kc * 8 + j;
-        x[j] = (r < ng && sidx < n_occ) ? phi[(long long)sidx * ng + r] : 0.f;
-      }
-      uint4 hi, lo;
-      split8(x, &hi, &lo);
-      *reinterpret_cast<uint4 *>(b_hi + canon_off(row, kc)) = hi;
-      *reinterpret_cast<uint4 *>(b_lo + canon_off(row, kc)) = lo;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    tma_pending = false;
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
@@ -405,11 +418,17 @@ __global__ void __launch_bounds__(kUmThreads)
       }
       mma_commit(smem_u32(&mbar));
     }
+    ++mma_issued;
+    if (!__syncthreads_and(mbar_wait(smem_u32(&mbar), (uint32_t)(it & 1)))) {
+      ok = false;
+      break;
+    }
   }
-  if (ok && n_iter > 0) ok = __syncthreads_and(mbar_wait(smem_u32(&mbar), (uint32_t)((n_iter - 1) & 1)));
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(err, 1);
-    mbar_wait(smem_u32(&mbar), (uint32_t)((n_iter - 1) & 1));
+    // copies and MMAs still in flight must finish before shared and tensor memory are released
+    if (tma_pending) tma_bar_wait(&tbar, (unsigned)((mma_issued) & 1));
+    if (mma_issued > 0) mbar_wait(smem_u32(&mbar), (uint32_t)((mma_issued - 1) & 1));
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   // Epilogue, in two halves of 128 grid points: the accumulator rows (m = 2c + h) are staged in the
@@ -501,16 +520,37 @@ __global__ void __launch_bounds__(kUmThreads)
 // grid-point tiles of the tensor-core cleaning update (rows of its norm partials)
 long long umma_clean_update_tiles(long long ng) { return (ng + kCuN - 1) / kCuN; }
 
-void launch_umma_clean_update(const double *ov, int n_cols, const float *phi, int n_occ, long long ng,
-                              float *d_interleaved, const float *a_interleaved, int L, double *npart, int *err,
-                              cudaStream_t s) {
-  const int M = 2 * n_cols;
-  const size_t smem = (size_t)2 * (kUmM + kCuN) * kUmBK * 2;
-  cudaFuncSetAttribute(k_umma_clean_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((unsigned)umma_clean_update_tiles(ng), (M + kUmM - 1) / kUmM);
-  k_umma_clean_update<<<grid, kUmThreads, smem, s>>>(ov, M, phi, n_occ, ng, d_interleaved, a_interleaved, L,
-                                                     npart, err);
+static int kchunks(int n_occ) { return (n_occ + kUmBK - 1) / kUmBK; }
+
+size_t umma_update_phi_bytes(long long ng, int n_occ) {
+  return (size_t)umma_clean_update_tiles(ng) * kchunks(n_occ) * kCanB;
+}
+size_t umma_update_o_bytes(int n_cols, int n_occ) {
+  return (size_t)((2 * n_cols + kUmM - 1) / kUmM) * kchunks(n_occ) * kCanA;
+}
+
+void umma_prepare_update_phi(const float *phi, int n_occ, long long ng, uint8_t *phi_can, cudaStream_t s) {
+  const long long tiles = umma_clean_update_tiles(ng);
+  const long long threads = tiles * kchunks(n_occ) * kCuN * 8;
+  k_canon_tiles<kCuN, SrcColsF32><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      SrcColsF32{phi, ng, n_occ}, tiles, kchunks(n_occ), phi_can);
   count_launch(1);
+}
+
+void launch_umma_clean_update(const double *ov, int n_cols, const uint8_t *phi_can, int n_occ, long long ng,
+                              float *d_interleaved, const float *a_interleaved, int L, double *npart,
+                              uint8_t *o_can, int *err, cudaStream_t s) {
+  const int M = 2 * n_cols;
+  const long long m_tiles = (M + kUmM - 1) / kUmM;
+  const long long threads = m_tiles * kchunks(n_occ) * kUmM * 8;
+  k_canon_tiles<kUmM, SrcRowsF64><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      SrcRowsF64{ov, M, n_occ}, m_tiles, kchunks(n_occ), o_can);
+  const size_t smem = (size_t)kCanA + kCanB;
+  cudaFuncSetAttribute(k_umma_clean_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)umma_clean_update_tiles(ng), (unsigned)m_tiles);
+  k_umma_clean_update<<<grid, kUmThreads, smem, s>>>(o_can, M, phi_can, kchunks(n_occ), ng, d_interleaved,
+                                                     a_interleaved, L, npart, err);
+  count_launch(2);
 }
 
 // tile width for Nn output columns: multiple of 16, at most 256
