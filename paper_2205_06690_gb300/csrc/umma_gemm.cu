@@ -436,8 +436,10 @@ __global__ void __launch_bounds__(kUmThreads)
   // columns with coalesced float2 accesses and reduces their norm sums.
   constexpr int kHalf = 128, kLd = kHalf + 1;
   float *Dsm = reinterpret_cast<float *>(smem);  // kUmM x kLd floats (66 KB) inside the operand buffer
-  __shared__ double colsum[kUmM / 2][2];
-  for (int i = threadIdx.x; i < kUmM; i += blockDim.x) colsum[i >> 1][i & 1] = 0.0;
+  // per-tile sums stay in FP32 (256 points): a warp-wide FP64 instruction occupies this GPU's narrow
+  // FP64 pipe for many cycles even with one active lane
+  __shared__ float colsum[kUmM / 2][2];
+  for (int i = threadIdx.x; i < kUmM; i += blockDim.x) colsum[i >> 1][i & 1] = 0.f;
   const int c0 = m0 / 2;
   for (int half = 0; half < kCuN / kHalf && ok; ++half) {
     __syncthreads();
@@ -476,8 +478,7 @@ __global__ void __launch_bounds__(kUmThreads)
       for (int i = 0; i < CB; ++i) {
         const int cl = cb + i, c = c0 + cl;
         float2 *dc = reinterpret_cast<float2 *>(d) + (long long)c * ng;
-        // FP32 sums over the 128 points of the half (the FP64 pipe of this GPU is too slow for
-        // per-point work); they are carried on in FP64 per tile and across tiles
+        // FP32 sums over the points of the tile; FP64 from the per-tile partials on
         float v1 = 0.f, v2 = 0.f;
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
@@ -498,8 +499,8 @@ __global__ void __launch_bounds__(kUmThreads)
           v2 += __shfl_xor_sync(0xffffffffu, v2, o);
         }
         if (lane == 0) {
-          colsum[cl][0] += (double)v1;
-          colsum[cl][1] += (double)v2;
+          colsum[cl][0] += v1;
+          colsum[cl][1] += v2;
         }
       }
     }
@@ -508,8 +509,8 @@ __global__ void __launch_bounds__(kUmThreads)
   for (int cl = threadIdx.x; cl < kUmM / 2; cl += blockDim.x) {
     const int c = c0 + cl;
     if (ok && c < n_cols) {
-      npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = colsum[cl][0];
-      npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = colsum[cl][1];
+      npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = (double)colsum[cl][0];
+      npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = (double)colsum[cl][1];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
