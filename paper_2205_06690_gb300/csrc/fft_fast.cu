@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
   const bool keep = pa.po.keep != 0.0;
   const int n_h = (2 * item + 1 < pa.po.n_out) ? 2 : 1;
   constexpr int UB = 8;
-#pragma unroll 2
+#pragma unroll 1  // code size: the unrolled epilogue missed the instruction cache
   for (int k0 = 0; k0 < N; k0 += UB) {
     C v[UB];
     T old[UB][2];
