@@ -540,6 +540,22 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   }
   const double pair_bytes = (double)L * ng * sizeof(C);
   const int chunk_pairs = std::max(1, std::min(P, (int)(ctx->l2_chunk_bytes / pair_bytes)));
+  // the eta0 set's round trip of step n, on the auxiliary stream once the pair batch of the step
+  // before has finished reading the buffer it overwrites
+  auto eta0_step = [&](const C *a_in, C *a_out, const C2<T> *pv) -> int {
+    XfwdArgs<T> xa{};
+    xa.mode = XF_PHASE_A;
+    xa.n_items = L;
+    xa.in = a_in;
+    xa.out = a_out;
+    xa.pv = pv;
+    CK(cudaEventRecord(ctx->ev_start, st));
+    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_start, 0));
+    round_trip_orbitals<T>(ctx, g, xa, a_out, L, nullptr, L, nullptr, ctx->aux, RT_ALL);
+    CK(cudaEventRecord(ctx->ev_a, ctx->aux));
+    return SBSE_OK;
+  };
+  bool eta0_issued = false;  // the eta0 round trip of this step was issued during the last Poisson
   for (int n = 0; n < Nt; ++n) {
     bool pending = n > 0;
     if (M > 0 && n % M == 0) {
@@ -579,12 +595,12 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       clk_end(ctx, c0);
       goto poisson_step;
     }
-    // the eta0 set (small launches) runs on the auxiliary stream, concurrently with the first two
-    // passes of the pair batch; the pairs' inverse pass (which needs the new eta0) waits for it
-    CK(cudaEventRecord(ctx->ev_start, st));
-    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_start, 0));
-    round_trip_orbitals<T>(ctx, g, xa, anext, L, nullptr, L, nullptr, ctx->aux, RT_ALL);
-    CK(cudaEventRecord(ctx->ev_a, ctx->aux));
+    // the eta0 set (small launches) runs on the auxiliary stream: issued during the previous
+    // step's Poisson solve (latency-bound, SMs to spare) unless a cleaning came in between, else
+    // here, concurrently with the first two passes of the pair batch; the pairs' inverse pass
+    // (which needs the new eta0) waits for it
+    if (!eta0_issued && (rc = eta0_step(acur, anext, xa.pv))) return rc;
+    eta0_issued = false;
     // the three passes run over chunks of pairs (SBSE_OPT_CHUNK_MB, default: all pairs at once)
     for (int p0 = 0; p0 < P; p0 += chunk_pairs) {
       const int pc = std::min(chunk_pairs, P - p0);
@@ -604,6 +620,12 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     }
     CHECK_LAUNCH("step");
     clk_end(ctx, c0);
+    if (n + 1 < Nt && !(M > 0 && (n + 1) % M == 0)) {
+      // next step's eta0 round trip: reads this step's new eta0 (anext), overwrites acur, which
+      // the pair batch above has finished reading; no cleaning in between, so its phase is full
+      if ((rc = eta0_step(anext, acur, g.pv_dt))) return rc;
+      eta0_issued = true;
+    }
   poisson_step:
     size_t c1 = 0;
     clk_begin(ctx, 1, &c1);
