@@ -326,6 +326,17 @@ def main():
     torch.cuda.synchronize()
     a_build_ms = ta0.elapsed_time(ta1)
 
+    # absorption spectrum from A (Sec. II.C, Chebyshev expansion; outside the timed step)
+    ev_ha = 1.0 / 27.211386245988
+    omega = np.linspace(0.0, 3.0, 1000)
+    n_terms = 4096
+    ctx.absorption(0, n_terms, 0.08 * ev_ha, omega)  # warm-up
+    torch.cuda.synchronize()
+    t_abs = time.perf_counter()
+    sig_abs, _ = ctx.absorption(0, n_terms, 0.08 * ev_ha, omega)
+    absorption = {"ms": 1e3 * (time.perf_counter() - t_abs), "n_terms": n_terms, "n_omega": len(omega),
+                  "broadening_ev": 0.08, "axis": "x", "peak_omega_ha": float(omega[int(np.argmax(sig_abs))])}
+
     # the plain FP64 GPU path on the same workload (shortened propagation, scaled to n_steps):
     # the comparator of the mixed path
     fp64 = None
@@ -446,6 +457,7 @@ def main():
         "gpu_launches": launches,
         "roofline": roofline,
         "a_build_ms": a_build_ms,
+        "absorption": absorption,
         "phase_ms_per_step": {str(k): v[0] / args.steps for k, v in phase.items()},
         "excitons_ha": [float(x) for x in ev],
         "fp64_gpu_path": fp64,

@@ -155,6 +155,23 @@ int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out);
  * Requires sbse_build_A. Errors: INVALID_ARG, NOT_READY, UNSUPPORTED, CUDA. */
 int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs);
 
+/* Absorption spectrum from A by a Chebyshev expansion (Sec. II.C, electron-hole basis, the
+ * paragraph after Eq. 18): sigma(omega) = omega <f0| G_s(A - omega) |f0>, the dipole correlation
+ * with the delta function smoothed by a normalised Gaussian G_s of standard deviation
+ * `broadening` (Ha) and the start vector f0_ia = <phi_a| x |phi_i> (x along `axis`: 0 = x, 1 = y,
+ * 2 = z, measured from the box centre; index ia = i * n_c + a). A is scaled to
+ * A~ = (A - c) / w from its Gershgorin bounds [lo, hi] (c = (lo + hi) / 2, w = 1.01 (hi - lo) / 2);
+ * the residues R_n = <f0| T_n(A~) |f0>, n < n_terms, come from the Chebyshev recursion applied to
+ * f0 on the device, and the Gaussian's Chebyshev coefficients from Chebyshev-Gauss quadrature on
+ * n_terms nodes. All FP64. More terms resolve narrower broadenings: n_terms of several times
+ * w / broadening.
+ * omega: host, n_omega frequencies (Ha). sigma: host out, n_omega values. residues: optional host
+ * out, n_terms values (NULL: not returned). Requires sbse_build_A.
+ * Errors: INVALID_ARG (axis, n_terms outside [2, 65536], broadening <= 0, n_omega outside
+ * [1, 2^24], NULL arrays), NOT_READY, OOM, NUMERIC (non-finite result), CUDA. */
+int sbse_absorption(sbse_ctx *ctx, int axis, int n_terms, double broadening, int n_omega,
+                    const double *omega, double *sigma, double *residues);
+
 /* Allocation-free variant of sbse_spectrum, for callers that cannot allocate device memory (for
  * example a host framework whose memory pool has reserved the whole GPU, or code that must not
  * trigger an allocation once it runs). The paper has no counterpart: it is an interface addition.

@@ -92,6 +92,7 @@ def load() -> C.CDLL:
         "sbse_set_W": (i, [vp, i, ip, ip, dp]),
         "sbse_get_W": (i, [vp, i, ip, ip, dp]),
         "sbse_spectrum": (i, [vp, i, dp, dp]),
+        "sbse_absorption": (i, [vp, i, i, d, i, dp, dp, dp]),
         "sbse_last_error": (C.c_char_p, [vp]),
         "sbse_get_stream": (i, [vp, C.POINTER(vp)]),
         "sbse_profile": (i, [vp, i]),
@@ -240,6 +241,16 @@ def sbse_spectrum(ctx, k: int):
     return ev
 
 
+def sbse_absorption(ctx, axis: int, n_terms: int, broadening: float, omega):
+    """sigma(omega) (Sec. II.C) and the Chebyshev residues R_n; see include/sbse.h."""
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1))
+    sig = np.empty_like(om)
+    res = np.empty(n_terms, dtype=np.float64)
+    _check(ctx, load().sbse_absorption(ctx, axis, n_terms, float(broadening), len(om), _dptr(om),
+                                       _dptr(sig), _dptr(res)))
+    return sig, res
+
+
 def sbse_get_stream(ctx) -> int:
     s = C.c_void_p()
     _check(ctx, load().sbse_get_stream(ctx, C.byref(s)))
@@ -367,3 +378,6 @@ class Context:
 
     def spectrum(self, k):
         return sbse_spectrum(self.h, k)
+
+    def absorption(self, axis, n_terms, broadening, omega):
+        return sbse_absorption(self.h, axis, n_terms, broadening, omega)

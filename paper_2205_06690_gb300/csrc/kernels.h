@@ -168,6 +168,17 @@ size_t umma_update_phi_bytes(long long ng, int n_occ);
 size_t umma_update_o_bytes(int n_cols, int n_occ);
 void umma_prepare_update_phi(const float *phi, int n_occ, long long ng, uint8_t *phi_can, cudaStream_t s);
 
+// ---- absorption spectrum by a Chebyshev expansion of A (spectrum.cu)
+struct SpectrumBufs {
+  double *f0, *cw, *v[3], *prod, *R, *D, *omega, *sigma;
+};
+size_t spectrum_work_bytes(int n, int n_terms, int n_omega);
+SpectrumBufs spectrum_bufs(double *work, int n, int n_terms, int n_omega);
+// the caller fills b.omega (n_omega frequencies) before; b.sigma and b.R (n_terms residues) after
+void launch_absorption(const SpectrumBufs &b, const double *phi_o, const double *phi_c, int n_o, int n_c, int N,
+                       double h, double box, double dV, const double *A, int axis, int n_terms, double s,
+                       int n_omega, cudaStream_t st);
+
 // ---- eigensolver (eig.cu)
 int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, cudaStream_t s);
 size_t eig_work_bytes(int n);

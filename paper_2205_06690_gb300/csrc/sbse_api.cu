@@ -89,7 +89,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -1081,6 +1081,40 @@ int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs) {
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < k; ++i)
     if (!isfinite(evals[i])) return fail(ctx, SBSE_ERR_NUMERIC, "eigenvalue is not finite");
+  return SBSE_OK;
+}
+
+int sbse_absorption(sbse_ctx *ctx, int axis, int n_terms, double broadening, int n_omega, const double *omega,
+                    double *sigma, double *residues) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ctx->have_A) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_build_A first");
+  if (axis < 0 || axis > 2) return fail(ctx, SBSE_ERR_INVALID_ARG, "axis must be 0 (x), 1 (y) or 2 (z)");
+  if (n_terms < 2 || n_terms > (1 << 16))
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "n_terms must be in [2, 65536]");
+  if (!(broadening > 0.0) || !isfinite(broadening))
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "broadening must be a positive finite energy (Ha)");
+  if (n_omega < 1 || n_omega > (1 << 24) || !omega || !sigma)
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "need 1 <= n_omega <= 2^24 and the omega and sigma arrays");
+  CK(cudaSetDevice(ctx->device));
+  const int n = ctx->n_o * ctx->n_c;
+  void *vp;
+  int rc;
+  if ((rc = ensure(ctx, WS_SPEC, spectrum_work_bytes(n, n_terms, n_omega), &vp))) return rc;
+  const SpectrumBufs b = spectrum_bufs((double *)vp, n, n_terms, n_omega);
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(b.omega, omega, (size_t)n_omega * sizeof(double), cudaMemcpyHostToDevice, st));
+  const double *phi_o = ctx->phi64 + (long long)(ctx->n_occ - ctx->n_o) * ctx->ng;
+  const double *phi_c = ctx->phi64 + (long long)ctx->n_occ * ctx->ng;
+  launch_absorption(b, phi_o, phi_c, ctx->n_o, ctx->n_c, ctx->N, ctx->h, ctx->box, ctx->dV, ctx->A, axis, n_terms,
+                    broadening, n_omega, st);
+  CHECK_LAUNCH("absorption");
+  CK(cudaMemcpyAsync(sigma, b.sigma, (size_t)n_omega * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (residues)
+    CK(cudaMemcpyAsync(residues, b.R, (size_t)n_terms * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int j = 0; j < n_omega; ++j)
+    if (!isfinite(sigma[j])) return fail(ctx, SBSE_ERR_NUMERIC, "spectrum is not finite");
   return SBSE_OK;
 }
 
