@@ -70,11 +70,11 @@ template <typename T, int N> constexpr size_t plane_smem() {
 
 // forward x and y FFTs of the PPB planes starting at plane offset `off` (= z0 N^2) of `item`, with
 // the fused pre-operation; S is the block's shared tile
-template <typename T, int N, bool PAIR>
+template <typename T, int N, bool PAIR, int PPB = kPPB<T, N>>
 __device__ __forceinline__ void fwd_planes(const GView<T> &g, const XfwdArgs<T> &a, long long item,
                                            long long off, C2<T> *S) {
   using C = C2<T>;
-  constexpr int PPB = kPPB<T, N>, LD = N + 1, NN = N * N, NT = PPB * N;
+  constexpr int LD = N + 1, NN = N * N, NT = PPB * N;
   const PreopItem<T> it = preop_item<T>(g, a, item);
   if constexpr (PAIR) {
     // the hot pre-operation of the pair batch: loads of 8 points are issued before any is used
@@ -166,15 +166,25 @@ __device__ __forceinline__ void fwd_planes(const GView<T> &g, const XfwdArgs<T> 
   }
 }
 
+// planes per block of the forward pass: the FP32 pair batch takes half the planes of the other
+// passes (smaller blocks: five resident per SM instead of two, 15 warps instead of 12, to hide
+// the L2 latency of its pre-operation's table loads)
+template <typename T, int N, bool PAIR> constexpr int fwd_ppb() {
+  return (PAIR && sizeof(T) == 4 && kPPB<T, N> % 2 == 0) ? kPPB<T, N> / 2 : kPPB<T, N>;
+}
+template <typename T, int N, bool PAIR> constexpr size_t fwd_smem() {
+  return (size_t)fwd_ppb<T, N, PAIR>() * N * (N + 1) * sizeof(C2<T>);
+}
+
 template <typename T, int N, bool PAIR>
-__global__ void __launch_bounds__(kPPB<T, N> * N)
+__global__ void __launch_bounds__(fwd_ppb<T, N, PAIR>() * N)
     k_plane_fwd(GView<T> g, XfwdArgs<T> a, long long planes_total) {
-  constexpr int PPB = kPPB<T, N>, NN = N * N;
+  constexpr int PPB = fwd_ppb<T, N, PAIR>(), NN = N * N;
   extern __shared__ unsigned char smem_raw[];
   // PPB divides N: the block's planes z0 .. z0 + PPB - 1 are contiguous inside one item
   const long long p0 = (long long)blockIdx.x * PPB;
   const long long item = p0 / N;
-  fwd_planes<T, N, PAIR>(g, a, item, (p0 - item * N) * NN, reinterpret_cast<C2<T> *>(smem_raw));
+  fwd_planes<T, N, PAIR, PPB>(g, a, item, (p0 - item * N) * NN, reinterpret_cast<C2<T> *>(smem_raw));
 }
 
 // one (x, y) column of one item: forward z FFT, multiplier, inverse z FFT (thread per column)
@@ -717,7 +727,8 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
 template <typename T, int N> static void set_attrs() {
   const int sm = (int)plane_smem<T, N>();
   cudaFuncSetAttribute(k_step_persistent<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_plane_fwd<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_fwd<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fwd_smem<T, N, true>());
   cudaFuncSetAttribute(k_plane_fwd<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_plane_inv<T, N, PI_DENSITY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -754,11 +765,14 @@ template <typename T> struct FastOps {
   template <int N> static void fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s) {
     if constexpr (!(sizeof(T) == 8 && N > 48)) {
       const long long planes = (long long)a.n_items * N;
-      const unsigned blocks = (unsigned)(planes / kPPB<T, N>);
-      if (a.mode == XF_PHASE_PAIR)
-        k_plane_fwd<T, N, true><<<blocks, kPPB<T, N> * N, plane_smem<T, N>(), s>>>(view(g), a, planes);
-      else
-        k_plane_fwd<T, N, false><<<blocks, kPPB<T, N> * N, plane_smem<T, N>(), s>>>(view(g), a, planes);
+      if (a.mode == XF_PHASE_PAIR) {
+        constexpr int P2 = fwd_ppb<T, N, true>();
+        k_plane_fwd<T, N, true><<<(unsigned)(planes / P2), P2 * N, fwd_smem<T, N, true>(), s>>>(view(g), a,
+                                                                                              planes);
+      } else {
+        k_plane_fwd<T, N, false><<<(unsigned)(planes / kPPB<T, N>), kPPB<T, N> * N, plane_smem<T, N>(), s>>>(
+            view(g), a, planes);
+      }
     }
   }
   template <int N> static void z(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s) {
