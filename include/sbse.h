@@ -218,6 +218,11 @@ int sbse_get_stream(const sbse_ctx *ctx, void **stream);
  * run as persistent kernels fed by bulk asynchronous copies (TMA) of their next planes or column
  * slabs; 0 uses the plain pass kernels. Results do not depend on it. */
 #define SBSE_OPT_TMA_PLANES 4
+/* SBSE_OPT_GRAPH (default 1): sbse_apply_W captures its time loop (all launches of all steps, on
+ * the context's two streams) into a CUDA graph and replays it on later calls whose buffers, sizes,
+ * parameters and options are unchanged, removing the host launch cost per step (which dominates
+ * on small grids). Not used while sbse_profile is enabled. Results do not depend on it. */
+#define SBSE_OPT_GRAPH 5
 int sbse_set_option(sbse_ctx *ctx, int option, int value);
 
 /* Number of CUDA kernel launches the library has issued in this process (all contexts), for

@@ -36,6 +36,7 @@ SBSE_OPT_TENSOR_CORES = 1
 SBSE_OPT_CHUNK_MB = 2
 SBSE_OPT_PERSISTENT = 3
 SBSE_OPT_TMA_PLANES = 4
+SBSE_OPT_GRAPH = 5
 
 _ERR_NAMES = {v: k for k, v in globals().items() if k.startswith("SBSE_ERR_")}
 

@@ -78,6 +78,10 @@ struct sbse_ctx {
   int persistent = 0;
   // inverse plane pass of the pair batch streamed by bulk copies (SBSE_OPT_TMA_PLANES)
   int tma_planes = 1;
+  // time loop of sbse_apply_W captured once and replayed as a CUDA graph (SBSE_OPT_GRAPH)
+  int use_graph = 1;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned long long> graph_key;
   // bytes of propagated orbitals per chunk of pairs (SBSE_OPT_CHUNK_MB); 0 = all pairs at once
   double l2_chunk_bytes = 1e30;
   // profiling
@@ -556,6 +560,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     return SBSE_OK;
   };
   bool eta0_issued = false;  // the eta0 round trip of this step was issued during the last Poisson
+  auto time_loop = [&]() -> int {
   for (int n = 0; n < Nt; ++n) {
     bool pending = n > 0;
     if (M > 0 && n % M == 0) {
@@ -639,6 +644,64 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       launch_flush_acc<T>(wacc, accT, (long long)P * ng, st);
     clk_end(ctx, c1);
     std::swap(acur, anext);
+  }
+  return SBSE_OK;
+  };
+  // The time loop's launches depend only on the values in this key (device buffers and tables,
+  // sizes, parameters, options); a call with an equal key replays the captured graph. Table and
+  // buffer contents are not part of it: they are written before the loop on every call.
+  auto ptr = [](const void *q) { return (unsigned long long)(uintptr_t)q; };
+  std::vector<unsigned long long> key = {
+      ptr(g.tw), ptr(g.kin), ptr(g.k2), ptr(g.v_loc), ptr(phi_T<T>(ctx)), (unsigned long long)ctx->N,
+      (unsigned long long)ctx->n_occ, (unsigned long long)ctx->tensor_cores, (unsigned long long)ctx->tma_planes,
+      (unsigned long long)(uintptr_t)d, (unsigned long long)(uintptr_t)a0,
+      (unsigned long long)(uintptr_t)a1, (unsigned long long)(uintptr_t)dn, (unsigned long long)(uintptr_t)pw,
+      (unsigned long long)(uintptr_t)wacc, (unsigned long long)(uintptr_t)accT, (unsigned long long)(uintptr_t)em1,
+      (unsigned long long)(uintptr_t)n0, (unsigned long long)(uintptr_t)cwork, (unsigned long long)(uintptr_t)phi_can,
+      (unsigned long long)(uintptr_t)g.pv_dt, (unsigned long long)(uintptr_t)g.pv_half, (unsigned long long)P,
+      (unsigned long long)L, (unsigned long long)Nt, (unsigned long long)M, (unsigned long long)p->feedback,
+      (unsigned long long)chunk_pairs, (unsigned long long)persistent, (unsigned long long)sizeof(T),
+      (unsigned long long)(uintptr_t)sq.items, (unsigned long long)(uintptr_t)sq.claim};
+  for (double v : {p->dt, p->gamma, p->alpha, ctx->dV}) {
+    unsigned long long b;
+    memcpy(&b, &v, sizeof b);
+    key.push_back(b);
+  }
+  bool replayed = false;
+  if (ctx->use_graph && !ctx->prof) {
+    if (ctx->graph_exec && ctx->graph_key == key) {
+      CK(cudaGraphLaunch(ctx->graph_exec, st));
+      replayed = true;
+    } else {
+      if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const int rc_loop = time_loop();
+        const cudaError_t e_end = cudaStreamEndCapture(st, &graph);
+        if (rc_loop) {
+          if (graph) cudaGraphDestroy(graph);
+          return rc_loop;
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (e_end == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+          ctx->graph_exec = exec;
+          ctx->graph_key = key;
+          CK(cudaGraphLaunch(exec, st));
+          replayed = true;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();  // a capture that could not be used leaves no error behind
+    }
+  }
+  if (!replayed) {
+    eta0_issued = false;
+    acur = a0;
+    anext = a1;
+    if ((rc = time_loop())) return rc;
   }
   {
     int h = 0;
@@ -840,6 +903,7 @@ void sbse_destroy(sbse_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   free_grid(ctx);
   free_scratch(ctx);
   dfree(ctx->flag);
@@ -1122,20 +1186,24 @@ int sbse_set_option(sbse_ctx *ctx, int option, int value) {
   if (!ctx) return SBSE_ERR_INVALID_ARG;
   if (option == SBSE_OPT_TENSOR_CORES) {
     ctx->tensor_cores = value != 0;
-    return SBSE_OK;
+      return SBSE_OK;
   }
   if (option == SBSE_OPT_PERSISTENT) {
     ctx->persistent = value != 0;
-    return SBSE_OK;
+      return SBSE_OK;
   }
   if (option == SBSE_OPT_TMA_PLANES) {
     ctx->tma_planes = value != 0;
+      return SBSE_OK;
+  }
+  if (option == SBSE_OPT_GRAPH) {
+    ctx->use_graph = value != 0;
     return SBSE_OK;
   }
   if (option == SBSE_OPT_CHUNK_MB) {
     if (value < 0) return fail(ctx, SBSE_ERR_INVALID_ARG, "chunk size must be >= 0");
     ctx->l2_chunk_bytes = value == 0 ? 1e30 : (double)value * (1 << 20);
-    return SBSE_OK;
+      return SBSE_OK;
   }
   return fail(ctx, SBSE_ERR_INVALID_ARG, "unknown option");
 }

@@ -272,3 +272,31 @@ def test_tma_streamed_inverse_pass_matches_plain_kernel(B, N, box):
                                       pairs=pairs)
         for k, pr in enumerate(pairs):
             assert rel_err(out[1][k].reshape(N, N, N), ref[pr]) < 2e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_replay_matches_direct_launches(B, prec):
+    """SBSE_OPT_GRAPH: the captured time loop replayed on later calls gives the results of direct
+    launches, bitwise; a new seed (coefficients are uploaded outside the graph) replays correctly,
+    and a new step count is captured afresh. 32^3 system, 5 pairs, cleaning every 4 steps."""
+    s = _small_system(32, 10.0, 5, 7, 6, 3, 4)
+    precision = B.SBSE_FP64 if prec == "fp64" else B.SBSE_MIXED
+    pairs = tdh.pair_list(3)[:5]
+
+    def run(graph, seeds, steps):
+        out = []
+        with B.Context(0, precision) as c:
+            B.sbse_set_option(c.h, B.SBSE_OPT_GRAPH, graph)
+            c.set_grid(s.N, s.box, s.v_loc)
+            c.set_orbitals(6, 3, 4, s.phi[:10], s.eps[:10], 0.5)
+            for seed, n in zip(seeds, steps):
+                prm = B.TDHParams(n_s=4, n_steps=n, clean_every=4, dt=0.05, gamma=0.1, alpha=1e-4, seed=seed)
+                out.append(c.apply_W(prm, pairs, copy_out=True))
+        return out
+
+    seeds, steps = [1, 1, 2, 2], [14, 14, 14, 9]
+    direct = run(0, seeds, steps)
+    graph = run(1, seeds, steps)
+    for a, b in zip(direct, graph):
+        assert np.array_equal(a, b)
+    assert np.array_equal(graph[0], graph[1]) and not np.array_equal(graph[1], graph[2])
