@@ -21,7 +21,8 @@ namespace sbse {
 
 constexpr int kUmM = 128;     // rows per tile (UMMA M)
 constexpr int kUmBK = 64;     // grid points per stage
-constexpr int kUmThreads = 128;
+constexpr int kUmThreads = 128;  // the cleaning update
+constexpr int kPgThreads = 256;  // the grid-sum GEMM: eight producer warps keep more loads in flight
 constexpr int kUmStages = 2;
 constexpr unsigned kWaitLimit = 1u << 26;
 
@@ -175,7 +176,7 @@ __device__ __forceinline__ void load_unit(int u, int units_a, const float *F, co
   }
 }
 
-template <int AMODE>
+template <int AMODE, int NTHR>
 __device__ __forceinline__ void produce_stage(uint8_t *st, int nt, const float *F, const int2 *xi, int M,
                                               int m0, const float *Y, int Nn, int n0, long long ng,
                                               long long k0, long long kend) {
@@ -187,7 +188,7 @@ __device__ __forceinline__ void produce_stage(uint8_t *st, int nt, const float *
   const int rr = lane & 7, kq = lane >> 3;
   const int units_a = (kUmM / 8) * 2, units_b = (nt / 8) * 2, total = units_a + units_b;
   const bool vec_ok = (ng & 3) == 0;  // 16-byte aligned rows
-  constexpr int W = kUmThreads / 32;
+  constexpr int W = NTHR / 32;
   for (int u0 = warp; u0 < total; u0 += W * kUB) {
     float x[kUB][8];
 #pragma unroll
@@ -212,7 +213,7 @@ __device__ __forceinline__ void produce_stage(uint8_t *st, int nt, const float *
 }
 
 template <int AMODE>
-__global__ void __launch_bounds__(kUmThreads)
+__global__ void __launch_bounds__(kPgThreads)
     k_umma_prod_gemm(const float *F, const int2 *xi, int M, const float *Y, int Nn, int nt, long long ng,
                      long long kchunk, double *part, int *err) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kUmThreads)
       break;
     }
     uint8_t *st = smem + s * stage_bytes;
-    produce_stage<AMODE>(st, nt, F, xi, M, m0, Y, Nn, n0, ng, kbeg + (long long)it * kUmBK, kend);
+    produce_stage<AMODE, kPgThreads>(st, nt, F, xi, M, m0, Y, Nn, n0, ng, kbeg + (long long)it * kUmBK, kend);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -284,12 +285,15 @@ __global__ void __launch_bounds__(kUmThreads)
     }
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
+  // epilogue: warp w reads the tensor-memory lanes of its quarter (w % 4) and half of the columns
+  const int quarter = warp & 3, chalf = warp >> 2;
+  const int c_lo = chalf == 0 ? 0 : ((nt / 16 + 1) / 2) * 16, c_hi = chalf == 0 ? ((nt / 16 + 1) / 2) * 16 : nt;
   if (ok && n_iter > 0) {
     const int lane = threadIdx.x & 31;
-    const int m = m0 + warp * 32 + lane;
-    for (int c = 0; c < nt; c += 16) {
+    const int m = m0 + quarter * 32 + lane;
+    for (int c = c_lo; c < c_hi; c += 16) {
       uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -305,9 +309,9 @@ __global__ void __launch_bounds__(kUmThreads)
     }
   } else if (n_iter == 0) {
     const int lane = threadIdx.x & 31;
-    const int m = m0 + warp * 32 + lane;
+    const int m = m0 + quarter * 32 + lane;
     if (m < M)
-      for (int c = 0; c < nt && n0 + c < Nn; ++c) part[((long long)blockIdx.x * M + m) * Nn + n0 + c] = 0.0;
+      for (int c = c_lo; c < c_hi && n0 + c < Nn; ++c) part[((long long)blockIdx.x * M + m) * Nn + n0 + c] = 0.0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -587,7 +591,7 @@ static int launch_umma(const float *F, const int2 *xi, int M, const float *Y, in
   const size_t smem = kUmStages * umma_stage_bytes(nt);
   cudaFuncSetAttribute(k_umma_prod_gemm<AMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)chunks, (M + kUmM - 1) / kUmM, (Nn + nt - 1) / nt);
-  k_umma_prod_gemm<AMODE><<<grid, kUmThreads, smem, s>>>(F, xi, M, Y, Nn, nt, ng, kc, work, err);
+  k_umma_prod_gemm<AMODE><<<grid, kPgThreads, smem, s>>>(F, xi, M, Y, Nn, nt, ng, kc, work, err);
   count_launch(1);
   launch_reduce_cols(work, (int)chunks, M * Nn, scale, out, s);
   return 0;
