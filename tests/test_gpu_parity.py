@@ -300,3 +300,38 @@ def test_graph_replay_matches_direct_launches(B, prec):
     for a, b in zip(direct, graph):
         assert np.array_equal(a, b)
     assert np.array_equal(graph[0], graph[1]) and not np.array_equal(graph[1], graph[2])
+
+
+def test_pair_shards_reassemble_the_single_run(B, tiny16):
+    """The multi-GPU split of a system (paper_2205_06690_gb300.shard): blocks of pairs propagated by
+    separate contexts (here two 'ranks' run in turn on one GPU, gathered on the host) and stored
+    with sbse_set_W give the W, A and excitons of one run over all pairs. FP64; the packing of two
+    pair densities per Poisson transform differs between the runs, hence 1e-12 and not bitwise."""
+    from paper_2205_06690_gb300 import shard
+    s = tiny16
+    p = s.preset
+    prm = B.TDHParams(n_s=10, n_steps=60, clean_every=10, dt=p.dt, gamma=p.gamma, alpha=p.alpha, seed=0)
+    pairs = shard.pair_list(p.n_o)
+
+    def ctx():
+        c = B.Context(0, B.SBSE_FP64)
+        c.set_grid(s.N, s.box, s.v_loc)
+        c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi[:p.n_occ + p.n_c], s.eps[:p.n_occ + p.n_c], p.scissor)
+        return c
+
+    with ctx() as c:
+        W_ref = c.apply_W(prm, pairs, copy_out=True)
+        A_ref = c.build_A()
+        ev_ref = c.spectrum(p.n_exc)
+    blocks = []
+    for r in range(2):
+        mine = [pairs[i] for i in shard.pair_block(len(pairs), r, 2)]
+        with ctx() as c:
+            blocks.append(c.apply_W(prm, mine, copy_out=True))
+    W = np.concatenate(blocks)
+    assert rel_err(W, W_ref) < 1e-12
+    with ctx() as c:
+        B.sbse_set_W(c.h, pairs, W)
+        A = c.build_A()
+        ev = c.spectrum(p.n_exc)
+    assert rel_err(A, A_ref) < 1e-12 and rel_err(ev, ev_ref) < 1e-12
