@@ -139,3 +139,46 @@ def test_stochastic_estimate_unbiased_and_converges_as_inverse_sqrt(tiny8):
         assert np.sqrt(np.sum((mean - w_det) ** 2)) < 0.45 * rms[n_s]
     slope = np.polyfit(np.log([2, 8, 32]), np.log([rms[2], rms[8], rms[32]]), 1)[0]
     assert -0.65 < slope < -0.35
+
+
+def test_eigenstate_under_the_split_operator_propagator(tiny8):
+    """With u = 0 an eigenstate of H0 = -1/2 Laplacian + V_loc stays itself up to a phase: after
+    t = 2, |<phi|psi>| = 1 - O(dt^4) and the phase error of exp(-i eps t) is O(dt^2) (Strang
+    splitting), i.e. it drops 4x when dt is halved."""
+    p, v, e, phi = tiny8
+    g = tdh.Grid(p.N, p.box)
+    s = 1
+    phase_err = []
+    for dt in (0.02, 0.01):
+        prop = tdh._Propagator(g, v, dt)
+        psi = phi[s].astype(np.complex128)
+        n = int(round(2.0 / dt))
+        for _ in range(n):
+            psi = prop.pv * prop.kinetic(prop.pv * psi)
+        ov = g.inner(phi[s], psi)
+        assert abs(abs(ov) - 1.0) < 1e-6
+        phase_err.append(abs(np.angle(ov * np.exp(1j * e[s] * n * dt))))
+    assert phase_err[1] < 1e-4 and 3.5 < phase_err[0] / phase_err[1] < 4.5
+
+
+def test_deterministic_w_pol_is_symmetric_and_screens(tiny8):
+    """Linear response of the full occupied set: <rho2|W^pol rho1> = <rho1|W^pol rho2> in the limit
+    dt -> 0 (the discrete time grid breaks the symmetry at O(dt^2): 4x less per halving), with and
+    without feedback; <rho|W^pol rho> < 0 and the screened <rho|v + W^pol|rho> is in (0, <rho|v rho>)."""
+    p, v, e, phi = tiny8
+    g = tdh.Grid(p.N, p.box)
+    r1, r2 = phi[0] * phi[1], phi[0] * phi[0] - phi[1] * phi[1]
+    for fb in (False, True):
+        asym = []
+        for dt in (0.04, 0.02):
+            pr = tdh.TDHParams(n_steps=int(round(4.0 / dt)), dt=dt, gamma=0.5, alpha=1e-6, clean_every=0,
+                               feedback=fb)
+            w1 = tdh.tdh_w_pol(g, v, phi[:2], r1, _det_coeff(2), pr)
+            w2 = tdh.tdh_w_pol(g, v, phi[:2], r2, _det_coeff(2), pr)
+            a, b = np.sum(r2 * w1) * g.dV, np.sum(r1 * w2) * g.dV
+            asym.append(abs(a - b) / max(abs(a), abs(b)))
+            for r, w in ((r1, w1), (r2, w2)):
+                pol = np.sum(r * w) * g.dV
+                bare = np.sum(r * tdh.coulomb_periodic(r, g)) * g.dV
+                assert pol < 0.0 and 0.0 < bare + pol < bare
+        assert asym[1] < 1e-4 and 3.5 < asym[0] / asym[1] < 4.5
