@@ -110,7 +110,7 @@ enum UmmaAMode { UA_PRODUCT = 0, UA_COMPLEX = 1 };
 // row (l & 7) of the group and core matrix kq = l >> 3, i.e. 8 consecutive points of one row. Each
 // warp loads kUB units before converting and storing any of them, so that several global loads per
 // lane are in flight.
-constexpr int kUB = 4;
+constexpr int kUB = 6;
 
 template <int AMODE>
 __device__ __forceinline__ void load_unit(int u, int units_a, const float *F, const int2 *xi, int M, int m0,
