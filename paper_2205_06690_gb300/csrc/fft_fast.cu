@@ -596,21 +596,29 @@ __global__ void __launch_bounds__(tma_z_rows(N) * N)
   }
 }
 
+// resident blocks per SM times SMs of the current device for a kernel and launch shape (0 if the
+// query fails)
+template <typename K> static long long resident_slots(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (long long)per_sm * sms;
+}
+
 template <int N>
 static bool zcol_tma(const GridTables<float> &g, float2 *d, int n_items, int mult, int *err, cudaStream_t s) {
   if constexpr (tma_inv_size(N)) {
     constexpr int Y = tma_z_rows(N);
     constexpr size_t sm = (size_t)Y * N * N * sizeof(float2);
     const long long units = (long long)n_items * (N / Y);
-    static int per_sm = -1, sms = 0;
-    if (per_sm < 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zcol_tma<N>, Y * N, sm);
-    }
-    if (per_sm < 1 || units < 1) return false;
-    const long long grid = units < (long long)per_sm * sms ? units : (long long)per_sm * sms;
+    // resident blocks of the whole GPU; function-local static: initialised once, thread-safe
+    static const long long slots = resident_slots(k_zcol_tma<N>, Y * N, sm);
+    if (slots < 1 || units < 1) return false;
+    const long long grid = units < slots ? units : slots;
     k_zcol_tma<N><<<(unsigned)grid, Y * N, sm, s>>>(view(g), d, n_items, mult, err);
     return true;
   }
@@ -623,16 +631,9 @@ static bool inv_density_tma(const GridTables<float> &g, float2 *d, int n_items, 
   if constexpr (tma_inv_size(N)) {
     constexpr int PPB = tma_inv_ppb(N);
     const long long units = (long long)(n_items / L) * (N / PPB);
-    static int per_sm = -1, sms = 0;
-    if (per_sm < 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plane_inv_density_tma<N>, PPB * N,
-                                                    tma_inv_smem<N>());
-    }
-    if (per_sm < 1 || units < 1) return false;
-    const long long grid = units < (long long)per_sm * sms ? units : (long long)per_sm * sms;
+    static const long long slots = resident_slots(k_plane_inv_density_tma<N>, PPB * N, tma_inv_smem<N>());
+    if (slots < 1 || units < 1) return false;
+    const long long grid = units < slots ? units : slots;
     k_plane_inv_density_tma<N><<<(unsigned)grid, PPB * N, tma_inv_smem<N>(), s>>>(view(g), d, a_next, dens, L,
                                                                                   n_items / L, err);
     return true;
