@@ -100,7 +100,7 @@ __device__ __forceinline__ void fwd_planes(const GView<T> &g, const XfwdArgs<T> 
         if (k0 + k < N) {
           const int l = threadIdx.x + (k0 + k) * NT;
           const int pl = l / NN, rem = l - pl * NN, y = rem / N, x = rem - y * N;
-          S[(pl * N + y) * LD + x] = pair_phase<T>(pv[k], ev[k], av[k], dv[k]);
+          S[(pl * N + y) * LD + x] = pair_phase<T>(pv[k], ev[k], av[k], renorm_value<T>(dv[k], av[k], it.cm1));
         }
       }
     }

@@ -42,6 +42,7 @@ template <typename T> struct XfwdArgs {
   const C2<T> *a;        // PAIR: a_cur
   const C2<T> *pv;       // A, PAIR: exp(-i V_loc tau) per grid point (tau = dt or dt/2)
   const C2<T> *em1;      // PAIR: exp(-i u tau) - 1 per pair (ng each); null -> u ignored
+  const double *cm1;     // PAIR: c - 1 per orbital of a renormalisation still to apply (null: none)
   int L;                 // PAIR: orbitals per pair
   const T *dn;           // PACK_DN: density per pair; slot s packs 2s (re) and 2s+1 (im)
   int n_dn;              // PACK_DN: number of densities
@@ -126,12 +127,15 @@ template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C
 // cleaning of Eq. (15): overlaps O[c][s] = dV sum_r phi_s d_c (c < P*L complex columns)
 // use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait;
 // dens != null: the renormalisation also writes the induced density of each pair (Eq. 11)
-// phi_can != null (FP32 only): the projection update on the tensor cores from pre-split orbitals
-template <typename T> void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
-                                        const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
-                                        double dV, double *work, size_t work_bytes, bool use_tc,
-                                        const uint8_t *phi_can, int *err, cudaStream_t s,
-                                        T *dens = nullptr);
+// phi_can != null (FP32 only): the projection update on the tensor cores from pre-split orbitals.
+// Returns c - 1 per orbital (device, P L values inside work). With defer, d is left unscaled: the
+// next forward pre-operation applies d <- c d + (c - 1) eta0 (XfwdArgs::cm1) and dens (required)
+// is computed from the scaled values on the fly.
+template <typename T> const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
+                                                 const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
+                                                 double dV, double *work, size_t work_bytes, bool use_tc,
+                                                 const uint8_t *phi_can, int *err, cudaStream_t s,
+                                                 T *dens = nullptr, bool defer = false);
 template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L);
 // d64 -> T conversion and FP64 -> T copies
 template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s);

@@ -49,6 +49,7 @@ template <typename T> struct PreopItem {
   const C2<T> *in;   // PHASE_A, PHASE_PAIR
   const C2<T> *a;    // PHASE_PAIR: eta0 of the same stochastic orbital
   const C2<T> *em1;  // PHASE_PAIR: E - 1 of the pair (null: no feedback)
+  T cm1;             // PHASE_PAIR: c - 1 of a deferred renormalisation (0: none)
   const C2<T> *pv;   // PHASE_A, PHASE_PAIR
   const T *r0, *r1, *r2, *r3;  // PACK_DN: r0 (re), r1 (im or null); PACK_PROD: r0 r1 (re), r2 r3 (im)
 };
@@ -66,6 +67,7 @@ __device__ __forceinline__ PreopItem<T> preop_item(const GView<T> &g, const Xfwd
     it.in = a.in + item * g.ng;
     it.a = a.a + (long long)ell * g.ng;
     it.em1 = a.em1 ? a.em1 + (long long)pair * g.ng : nullptr;
+    it.cm1 = a.cm1 ? (T)a.cm1[item] : T(0);
   } else if (a.mode == XF_PACK_DN) {
     it.r0 = a.dn + 2 * item * g.ng;
     it.r1 = (2 * item + 1 < a.n_dn) ? a.dn + (2 * item + 1) * g.ng : nullptr;
@@ -79,6 +81,11 @@ __device__ __forceinline__ PreopItem<T> preop_item(const GView<T> &g, const Xfwd
   return it;
 }
 
+// deferred renormalisation of a cleaning (Eq. 15 reading): d <- c d + (c - 1) eta0, cm1 = c - 1
+template <typename T> __device__ __forceinline__ C2<T> renorm_value(C2<T> dv, C2<T> av, T cm1) {
+  return C2<T>{(T(1) + cm1) * dv.x + cm1 * av.x, (T(1) + cm1) * dv.y + cm1 * av.y};
+}
+
 template <typename T>
 __device__ __forceinline__ C2<T> pair_phase(C2<T> pv, C2<T> em1, C2<T> av, C2<T> dv) {
   const C2<T> E = C2<T>{T(1) + em1.x, em1.y};
@@ -89,8 +96,11 @@ template <typename T>
 __device__ __forceinline__ C2<T> preop_at(const GView<T> &g, const PreopItem<T> &it, long long idx) {
   using C = C2<T>;
   if (it.mode == XF_PHASE_A) return cmul(it.pv[idx], it.in[idx]);
-  if (it.mode == XF_PHASE_PAIR)
-    return pair_phase<T>(it.pv[idx], it.em1 ? it.em1[idx] : C{T(0), T(0)}, it.a[idx], it.in[idx]);
+  if (it.mode == XF_PHASE_PAIR) {
+    const C av = it.a[idx];
+    return pair_phase<T>(it.pv[idx], it.em1 ? it.em1[idx] : C{T(0), T(0)}, av,
+                         renorm_value<T>(it.in[idx], av, it.cm1));
+  }
   if (it.mode == XF_PACK_DN) return C{it.r0[idx], it.r1 ? it.r1[idx] : T(0)};
   return C{it.r0[idx] * it.r1[idx], it.r2 ? it.r2[idx] * it.r3[idx] : T(0)};
 }

@@ -563,13 +563,15 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   auto time_loop = [&]() -> int {
   for (int n = 0; n < Nt; ++n) {
     bool pending = n > 0;
+    const double *cm1_pending = nullptr;
     if (M > 0 && n % M == 0) {
       size_t ck = 0;
       clk_begin(ctx, 2, &ck);
       if (pending) launch_half_phase<T>(g, acur, d, em1, P, L, st);
       pending = false;
-      launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
-                      ctx->tensor_cores != 0, phi_can, ctx->flag, st, dn);
+      // the renormalisation is applied by this step's forward pre-operation (one sweep of d less)
+      cm1_pending = launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
+                                    ctx->tensor_cores != 0, phi_can, ctx->flag, st, dn, true);
       CHECK_LAUNCH("clean");
       if ((rc = poisson<T>(ctx, g, dn, P, pw, nullptr, accT, wts[n], em1, 0.5 * p->dt))) return rc;
       clk_end(ctx, ck);
@@ -590,6 +592,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       xb.out = d;
       xb.a = acur;
       xb.em1 = em1;
+      xb.cm1 = cm1_pending;
       xb.L = L;
       xb.pv = xa.pv;
       sq.claim_base = (unsigned)(epoch * (unsigned long long)(sq.n_items + step_grid));
@@ -617,6 +620,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       xb.out = dc;
       xb.a = acur;
       xb.em1 = em1 ? em1 + (long long)p0 * ng : nullptr;
+      xb.cm1 = cm1_pending ? cm1_pending + (long long)p0 * L : nullptr;
       xb.L = L;
       xb.pv = pending ? g.pv_dt : g.pv_half;
       round_trip_orbitals<T>(ctx, g, xb, dc, pc * L, anext, L, dn + (long long)p0 * ng, st, RT_FWD_Z);

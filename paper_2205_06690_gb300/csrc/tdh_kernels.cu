@@ -481,6 +481,26 @@ __global__ void k_renorm_density(long long ng, C2<T> *d, const C2<T> *a, int L, 
   dens[(long long)pair * ng + r] = acc;
 }
 
+// the same densities for a deferred renormalisation: d is read, scaled in registers, not stored
+template <typename T>
+__global__ void k_density_renormed(long long ng, const C2<T> *d, const C2<T> *a, int L, const double *cm1v,
+                                   T *dens) {
+  extern __shared__ unsigned char sm_raw[];
+  T *cm1s = reinterpret_cast<T *>(sm_raw);
+  const int pair = blockIdx.y;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) cm1s[l] = (T)cm1v[(long long)pair * L + l];
+  __syncthreads();
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ng) return;
+  T acc = T(0);
+  for (int ell = 0; ell < L; ++ell) {
+    const C2<T> a0 = a[(long long)ell * ng + r];
+    const C2<T> dv = renorm_value<T>(d[((long long)pair * L + ell) * ng + r], a0, cm1s[ell]);
+    acc += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+  }
+  dens[(long long)pair * ng + r] = acc;
+}
+
 // Overlaps of the complex columns d_c with the occupied orbitals, split over chunks of grid
 // points: part[chunk][c][s] = sum_{r in chunk} (Re d_c(r), Im d_c(r)) phi_s(r). Tile of 64
 // columns x 64 states, 16 points per stage, 4 x 4 complex outputs per thread.
@@ -664,9 +684,10 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
 }
 
 template <typename T>
-void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
-                  int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
-                  bool use_tc, const uint8_t *phi_can, int *err, cudaStream_t s, T *dens) {
+const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
+                           int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
+                           bool use_tc, const uint8_t *phi_can, int *err, cudaStream_t s, T *dens,
+                           bool defer) {
   (void)work_bytes;
   const int n_cols = P * L;
   const long long kc = gemm_kchunk(g.ng);
@@ -700,7 +721,10 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
     launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
   }
   k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
-  if (dens) {
+  if (defer && dens) {
+    dim3 g3((unsigned)((g.ng + 255) / 256), P);
+    k_density_renormed<T><<<g3, 256, (size_t)L * sizeof(T), s>>>(g.ng, d, a, L, cm1, dens);
+  } else if (dens) {
     dim3 g3((unsigned)((g.ng + 255) / 256), P);
     k_renorm_density<T><<<g3, 256, (size_t)L * sizeof(T), s>>>(g.ng, d, a, L, cm1, dens);
   } else {
@@ -708,6 +732,7 @@ void launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<
     k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);
   }
   count_launch(3);
+  return cm1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -794,9 +819,9 @@ void init_fft_kernels() {
                                double, C2<T> *, cudaStream_t);                                     \
   template void launch_half_phase<T>(const GridTables<T> &, C2<T> *, C2<T> *, const C2<T> *, int, int, \
                                      cudaStream_t);                                              \
-  template void launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *, C2<T> *,     \
-                                int, int, const double *, double, double *, size_t, bool,          \
-                                const uint8_t *, int *, cudaStream_t, T *);                                                     \
+  template const double *launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *,      \
+                                         C2<T> *, int, int, const double *, double, double *, size_t, \
+                                         bool, const uint8_t *, int *, cudaStream_t, T *, bool);                                                     \
   template size_t clean_work_bytes<T>(long long, int, int, int);                                   \
   template void launch_convert<T>(const double *, T *, long long, cudaStream_t);
 
