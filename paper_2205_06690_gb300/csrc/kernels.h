@@ -128,14 +128,13 @@ template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C
 // use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait;
 // dens != null: the renormalisation also writes the induced density of each pair (Eq. 11)
 // phi_can != null (FP32 only): the projection update on the tensor cores from pre-split orbitals.
-// Returns c - 1 per orbital (device, P L values inside work). With defer, d is left unscaled: the
-// next forward pre-operation applies d <- c d + (c - 1) eta0 (XfwdArgs::cm1) and dens (required)
-// is computed from the scaled values on the fly.
+// Returns c - 1 per orbital (device, P L values inside work); d is left unscaled: the next forward
+// pre-operation applies d <- c d + (c - 1) eta0 (XfwdArgs::cm1), and dens (P n_g) receives the
+// induced densities of the rescaled orbitals.
 template <typename T> const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
                                                  const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
                                                  double dV, double *work, size_t work_bytes, bool use_tc,
-                                                 const uint8_t *phi_can, int *err, cudaStream_t s,
-                                                 T *dens = nullptr, bool defer = false);
+                                                 const uint8_t *phi_can, int *err, cudaStream_t s, T *dens);
 template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L);
 // d64 -> T conversion and FP64 -> T copies
 template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s);

@@ -571,7 +571,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       pending = false;
       // the renormalisation is applied by this step's forward pre-operation (one sweep of d less)
       cm1_pending = launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
-                                    ctx->tensor_cores != 0, phi_can, ctx->flag, st, dn, true);
+                                    ctx->tensor_cores != 0, phi_can, ctx->flag, st, dn);
       CHECK_LAUNCH("clean");
       if ((rc = poisson<T>(ctx, g, dn, P, pw, nullptr, accT, wts[n], em1, 0.5 * p->dt))) return rc;
       clk_end(ctx, ck);

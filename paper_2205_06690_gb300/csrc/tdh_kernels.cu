@@ -440,48 +440,11 @@ __global__ void k_cm1(int n_cols, int L, const double *sums /* [c][2], times dV 
   cm1[c] = -x / (sq * (1.0 + sq));
 }
 
-template <typename T>
-__global__ void k_renorm(long long ng, C2<T> *d, const C2<T> *a, int n_cols, int L, const double *cm1v) {
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = blockIdx.y;
-  if (r >= ng) return;
-  const int ell = c % L;
-  const T cm1 = (T)cm1v[c];
-  C2<T> *dp = d + (long long)c * ng + r;
-  const C2<T> a0 = a[(long long)ell * ng + r];
-  C2<T> dv = *dp;
-  dv.x = (T(1) + cm1) * dv.x + cm1 * a0.x;
-  dv.y = (T(1) + cm1) * dv.y + cm1 * a0.y;
-  *dp = dv;
-}
 
-// renormalisation fused with the induced density of the cleaned orbitals (Eq. 11): block = 256
-// points of one pair; c - 1 of the pair's L columns is converted to T once per block (a per-point
-// FP64 -> FP32 conversion would load the narrow FP64 pipe)
-template <typename T>
-__global__ void k_renorm_density(long long ng, C2<T> *d, const C2<T> *a, int L, const double *cm1v, T *dens) {
-  extern __shared__ unsigned char sm_raw[];
-  T *cm1s = reinterpret_cast<T *>(sm_raw);
-  const int pair = blockIdx.y;
-  for (int l = threadIdx.x; l < L; l += blockDim.x) cm1s[l] = (T)cm1v[(long long)pair * L + l];
-  __syncthreads();
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= ng) return;
-  T acc = T(0);
-  for (int ell = 0; ell < L; ++ell) {
-    const T cm1 = cm1s[ell];
-    const C2<T> a0 = a[(long long)ell * ng + r];
-    C2<T> *dp = d + ((long long)pair * L + ell) * ng + r;
-    C2<T> dv = *dp;
-    dv.x = (T(1) + cm1) * dv.x + cm1 * a0.x;
-    dv.y = (T(1) + cm1) * dv.y + cm1 * a0.y;
-    *dp = dv;
-    acc += T(2) * (T(2) * (a0.x * dv.x + a0.y * dv.y) + dv.x * dv.x + dv.y * dv.y);
-  }
-  dens[(long long)pair * ng + r] = acc;
-}
-
-// the same densities for a deferred renormalisation: d is read, scaled in registers, not stored
+// induced densities (Eq. 11) of the cleaned and rescaled orbitals, the rescaling d <- c d + (c-1) eta0
+// being applied in registers only (the next forward pre-operation applies it to d itself): block =
+// 256 points of one pair; c - 1 of the pair's L orbitals is converted to T once per block (a
+// per-point FP64 -> FP32 conversion would load the narrow FP64 pipe)
 template <typename T>
 __global__ void k_density_renormed(long long ng, const C2<T> *d, const C2<T> *a, int L, const double *cm1v,
                                    T *dens) {
@@ -686,8 +649,7 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
 template <typename T>
 const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
                            int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
-                           bool use_tc, const uint8_t *phi_can, int *err, cudaStream_t s, T *dens,
-                           bool defer) {
+                           bool use_tc, const uint8_t *phi_can, int *err, cudaStream_t s, T *dens) {
   (void)work_bytes;
   const int n_cols = P * L;
   const long long kc = gemm_kchunk(g.ng);
@@ -721,16 +683,8 @@ const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, 
     launch_reduce_cols(npart, (int)ptb, n_cols * 2, dV, sums, s);
   }
   k_cm1<<<(n_cols + 127) / 128, 128, 0, s>>>(n_cols, L, sums, n0, cm1);
-  if (defer && dens) {
-    dim3 g3((unsigned)((g.ng + 255) / 256), P);
-    k_density_renormed<T><<<g3, 256, (size_t)L * sizeof(T), s>>>(g.ng, d, a, L, cm1, dens);
-  } else if (dens) {
-    dim3 g3((unsigned)((g.ng + 255) / 256), P);
-    k_renorm_density<T><<<g3, 256, (size_t)L * sizeof(T), s>>>(g.ng, d, a, L, cm1, dens);
-  } else {
-    dim3 g3((unsigned)((g.ng + 255) / 256), n_cols);
-    k_renorm<T><<<g3, 256, 0, s>>>(g.ng, d, a, n_cols, L, cm1);
-  }
+  dim3 g3((unsigned)((g.ng + 255) / 256), P);
+  k_density_renormed<T><<<g3, 256, (size_t)L * sizeof(T), s>>>(g.ng, d, a, L, cm1, dens);
   count_launch(3);
   return cm1;
 }
@@ -821,7 +775,7 @@ void init_fft_kernels() {
                                      cudaStream_t);                                              \
   template const double *launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *,      \
                                          C2<T> *, int, int, const double *, double, double *, size_t, \
-                                         bool, const uint8_t *, int *, cudaStream_t, T *, bool);                                                     \
+                                         bool, const uint8_t *, int *, cudaStream_t, T *);                                                     \
   template size_t clean_work_bytes<T>(long long, int, int, int);                                   \
   template void launch_convert<T>(const double *, T *, long long, cudaStream_t);
 
