@@ -356,9 +356,17 @@ def main():
             f1.record(ext64)
             torch.cuda.synchronize()
             ms64 = f0.elapsed_time(f1) * n_steps / short
+            # A-build time of the FP64 path (FP64 CUDA-core contractions), A built once before
+            c64.build_A(copy_out=False)
+            f0.record(ext64)
+            c64.build_A(copy_out=False)
+            f1.record(ext64)
+            torch.cuda.synchronize()
+            a64_ms = f0.elapsed_time(f1)
         fp64 = {"value": P / (ms64 / 1e3), "unit": "W-applications/s",
                 "sample": f"all {P} pairs x {short} TDH steps, scaled to {n_steps}",
-                "mixed_speedup": (P / (ms_step / 1e3)) / (P / (ms64 / 1e3))}
+                "mixed_speedup": (P / (ms_step / 1e3)) / (P / (ms64 / 1e3)),
+                "a_build_ms": a64_ms, "a_build_speedup_mixed": a64_ms / a_build_ms}
 
     # learned form: FNO surrogate of the workload's shape (64^3, width 32, 12 modes, 4 layers)
     surrogate = None

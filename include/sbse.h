@@ -151,8 +151,12 @@ int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out);
 
 /* Lowest k eigenvalues of A (Eq. 1; the exciton energies, Ha), ascending, by an FP64
  * Householder tridiagonalisation and Sturm bisection on the device.
- * evals: host, k doubles. evecs: must be NULL (eigenvectors are not provided by this build).
- * Requires sbse_build_A. Errors: INVALID_ARG, NOT_READY, UNSUPPORTED, CUDA. */
+ * evals: host, k doubles. evecs: optional host (n_o n_c) x k doubles, row-major (component ia of
+ * exciton j at evecs[ia * k + j]): orthonormal eigenvectors by inverse iteration on the
+ * tridiagonal matrix (vectors of eigenvalues closer than 1e-3 |T| orthogonalised against each
+ * other) and the Householder back-transformation, each with its largest-magnitude component
+ * positive; NULL returns eigenvalues only. For degenerate excitons only the spanned subspace is
+ * defined. Requires sbse_build_A. Errors: INVALID_ARG, NOT_READY, OOM, NUMERIC, CUDA. */
 int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs);
 
 /* Absorption spectrum from A by a Chebyshev expansion (Sec. II.C, electron-hole basis, the

@@ -236,10 +236,15 @@ def sbse_build_A(ctx, terms: int = SBSE_EXCHANGE | SBSE_DIRECT, n: int | None = 
     return out
 
 
-def sbse_spectrum(ctx, k: int):
+def sbse_spectrum(ctx, k: int, n: int | None = None):
+    """Lowest k excitons; given n = n_o n_c, also their eigenvectors as an (n, k) array."""
     ev = np.empty(k)
-    _check(ctx, load().sbse_spectrum(ctx, k, _dptr(ev), None))
-    return ev
+    if n is None:
+        _check(ctx, load().sbse_spectrum(ctx, k, _dptr(ev), None))
+        return ev
+    vec = np.empty((n, k))
+    _check(ctx, load().sbse_spectrum(ctx, k, _dptr(ev), _dptr(vec)))
+    return ev, vec
 
 
 def sbse_absorption(ctx, axis: int, n_terms: int, broadening: float, omega):
@@ -377,8 +382,8 @@ class Context:
     def build_A(self, terms=SBSE_EXCHANGE | SBSE_DIRECT, copy_out=True):
         return sbse_build_A(self.h, terms, self.n if copy_out else None)
 
-    def spectrum(self, k):
-        return sbse_spectrum(self.h, k)
+    def spectrum(self, k, vectors=False):
+        return sbse_spectrum(self.h, k, self.n if vectors else None)
 
     def absorption(self, axis, n_terms, broadening, omega):
         return sbse_absorption(self.h, axis, n_terms, broadening, omega)

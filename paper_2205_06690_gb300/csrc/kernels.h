@@ -185,5 +185,9 @@ void launch_absorption(const SpectrumBufs &b, const double *phi_o, const double 
 // ---- eigensolver (eig.cu)
 int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, cudaStream_t s);
 size_t eig_work_bytes(int n);
+// the same eigenvalues with their eigenvectors (device, row-major n x k, largest component positive)
+int launch_eig_vectors(const double *A, int n, int k, double *evals_dev, double *evecs_dev, double *work,
+                       cudaStream_t s);
+size_t eig_vectors_work_bytes(int n, int k);
 
 }  // namespace sbse

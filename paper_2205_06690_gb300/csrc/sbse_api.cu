@@ -1134,10 +1134,27 @@ int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs) {
   if (!ctx->have_A) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_build_A first");
   const int n = ctx->n_o * ctx->n_c;
   if (!evals || k < 1 || k > n) return fail(ctx, SBSE_ERR_INVALID_ARG, "need evals and 1 <= k <= n_o n_c");
-  if (evecs) return fail(ctx, SBSE_ERR_UNSUPPORTED, "eigenvectors are not provided by this build");
   CK(cudaSetDevice(ctx->device));
   void *vp;
   int rc;
+  if (evecs) {
+    const size_t wb = (eig_vectors_work_bytes(n, k) + 255) / 256 * 256;
+    if ((rc = ensure(ctx, WS_EIG, wb + (size_t)(k + (size_t)n * k) * sizeof(double), &vp))) return rc;
+    double *ev = (double *)((char *)vp + wb), *vec = ev + k;
+    size_t c4 = 0;
+    clk_begin(ctx, 4, &c4);
+    launch_eig_vectors(ctx->A, n, k, ev, vec, (double *)vp, ctx->stream);
+    CHECK_LAUNCH("eig vectors");
+    clk_end(ctx, c4);
+    CK(cudaMemcpyAsync(evals, ev, k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(evecs, vec, (size_t)n * k * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (long long i = 0; i < (long long)n * k; ++i)
+      if (!isfinite(evecs[i])) return fail(ctx, SBSE_ERR_NUMERIC, "eigenvector is not finite");
+    for (int i = 0; i < k; ++i)
+      if (!isfinite(evals[i])) return fail(ctx, SBSE_ERR_NUMERIC, "eigenvalue is not finite");
+    return SBSE_OK;
+  }
   if ((rc = ensure(ctx, WS_EIG, eig_work_bytes(n) + (size_t)(k + 1) * sizeof(double), &vp))) return rc;
   double *ev = (double *)vp + (long long)n * n + 2 * n;
   size_t c4 = 0;

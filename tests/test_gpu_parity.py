@@ -147,12 +147,12 @@ def test_call_order_and_argument_errors(B, tiny16):
             c.apply_W(B.TDHParams(n_s=0), [(0, 0)])
         assert e.value.code == B.SBSE_ERR_INVALID_ARG
         c.build_A(B.SBSE_EXCHANGE)
-        import ctypes
         ev = np.empty(2)
-        ec = np.empty(16)
-        rc = B.load().sbse_spectrum(c.h, 2, B._dptr(ev), B._dptr(ec))
-        assert rc == B.SBSE_ERR_UNSUPPORTED
-        assert ctypes is not None
+        ec = np.empty(16)  # eigenvectors: (n_o n_c) x k = 8 x 2, row-major
+        assert B.load().sbse_spectrum(c.h, 2, B._dptr(ev), B._dptr(ec)) == B.SBSE_OK
+        X = ec.reshape(8, 2)
+        assert np.max(np.abs(X.T @ X - np.eye(2))) < 1e-10
+        assert B.load().sbse_spectrum(c.h, 0, B._dptr(ev), None) == B.SBSE_ERR_INVALID_ARG
 
 
 @pytest.fixture(scope="module")

@@ -76,3 +76,41 @@ def test_absorption_argument_errors(B, tiny16):
                 c.absorption(*args, [0.5])
         sig, R = c.absorption(1, 2, 0.01, [0.5, 1.0])
         assert np.all(np.isfinite(sig)) and R.shape == (2,)
+
+
+def _small(N, box, n_wells, seed, n_occ, n_o, n_c):
+    import sbse_inputs as si
+    return si.make_system(si.model_system.Preset(f"v{N}", N=N, box=box, n_wells=n_wells, seed=seed,
+                                                 n_occ=n_occ, n_o=n_o, n_c=n_c))
+
+
+@pytest.mark.parametrize("case", ["tiny16_k4", "tiny16_all", "n32_k10"])
+def test_exciton_eigenvectors(B, tiny16, case):
+    """sbse_spectrum with eigenvectors (FP64 A with the exchange term): A x_j = lambda_j x_j to
+    1e-10 |A|, orthonormal to 1e-10, eigenvalues equal to those of numpy's eigh of the same matrix,
+    vectors equal to eigh's up to the sign convention (largest component positive) wherever the
+    eigenvalue is separated from its neighbours."""
+    if case.startswith("tiny16"):
+        s, n_occ, n_o, n_c = tiny16, 4, 2, 4
+        k = 4 if case == "tiny16_k4" else 8
+    else:
+        s, n_occ, n_o, n_c, k = _small(32, 10.0, 6, 3, 8, 4, 8), 8, 4, 8, 10
+    with B.Context(0, B.SBSE_FP64) as c:
+        c.set_grid(s.N, s.box, s.v_loc)
+        c.set_orbitals(n_occ, n_o, n_c, s.phi[:n_occ + n_c], s.eps[:n_occ + n_c], 0.5)
+        A = c.build_A(B.SBSE_EXCHANGE)
+        ev, X = c.spectrum(k, vectors=True)
+        ev2, X2 = c.spectrum(k, vectors=True)
+    n = n_o * n_c
+    assert X.shape == (n, k) and np.array_equal(X, X2) and np.array_equal(ev, ev2)
+    scale = np.max(np.abs(A))
+    assert np.max(np.abs(A @ X - X * ev[None, :])) < 1e-10 * scale
+    assert np.max(np.abs(X.T @ X - np.eye(k))) < 1e-10
+    E, U = np.linalg.eigh(0.5 * (A + A.T))
+    assert np.max(np.abs(ev - E[:k])) < 1e-10 * scale
+    for j in range(k):
+        gap = min(abs(E[j] - E[q]) for q in range(n) if q != j)
+        if gap > 1e-6 * scale:
+            u = U[:, j] * np.sign(U[np.argmax(np.abs(U[:, j])), j])
+            assert np.max(np.abs(X[:, j] - u)) < 1e-8
+        assert X[np.argmax(np.abs(X[:, j])), j] > 0
