@@ -701,10 +701,11 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       cudaGetLastError();  // a capture that could not be used leaves no error behind
     }
   }
-  if (!replayed) {
+  if (!replayed) {  // (a capture that could not be used only recorded work: start the loop afresh)
     eta0_issued = false;
     acur = a0;
     anext = a1;
+    epoch = 0;
     if ((rc = time_loop())) return rc;
   }
   {
