@@ -125,7 +125,9 @@ int sbse_coefficients(uint64_t seed, int n_s, int n_occ, int dist, double *out);
  * coeff: optional host n_s x n_occ matrix c[l][s]; NULL draws it from p->seed, p->coeff_dist.
  * w_out: optional host buffer n_pairs x n^3 doubles receiving W_ij; NULL keeps the results on
  *        the device only. Results are always kept on the device for sbse_build_A.
- * Requires sbse_set_orbitals. Errors: INVALID_ARG, NOT_READY, OOM, NUMERIC, CUDA. */
+ * Requires sbse_set_orbitals. Errors: INVALID_ARG, NOT_READY, OOM, NUMERIC, DEVICE_TIMEOUT (a
+ * bounded device-side wait of a bulk-copy, tensor-core or persistent kernel ran out; results are
+ * not valid), CUDA. */
 int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int *pi,
                  const int *pj, const double *coeff, double *w_out);
 
