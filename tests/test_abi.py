@@ -48,3 +48,19 @@ def test_host_side_argument_errors(lib):
     assert lib.sbse_set_grid(None, 16, 8.0, None) == B.SBSE_ERR_INVALID_ARG
     assert lib.sbse_apply_W(None, None, 0, None, None, None, None) == B.SBSE_ERR_INVALID_ARG
     lib.sbse_destroy(None)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/sbse.h compiles as C99 (no C++ types cross the boundary) and as C++."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use.c"
+    src.write_text('#include "sbse.h"\nint main(void) { sbse_ctx *c = 0; (void)c; return 0; }\n')
+    for lang in (["-std=c99", "-x", "c"], ["-std=c++17", "-x", "c++"]):
+        r = subprocess.run([cc, *lang, "-Wall", "-Werror", "-I", os.path.join(root, "include"), "-c", str(src),
+                            "-o", str(tmp_path / "use.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
