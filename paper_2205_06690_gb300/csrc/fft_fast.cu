@@ -847,7 +847,9 @@ template <typename T> int step_tiles_per_orbital(int N) {
 }
 
 template <typename T> bool fast_supported(int N) {
-  // FP64 pencils of 64 would not fit in the register file
+  // FP64 pencils of 64 would not fit in the register file; 80 and 96 take the FP32 lane-pair
+  // passes of fft_split.cu
+  if (split_size(N)) return sizeof(T) == 4;
   for (int i = 0; i < kRegCount; ++i)
     if (kRegSizes[i] == N) return !(sizeof(T) == 8 && N > 48);
   return false;
@@ -862,6 +864,13 @@ template <typename T> void init_fast_kernels() {
 }
 
 template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (split_size(g.N)) {
+      launch_plane_fwd2(g, a, s);
+      count_launch(1);
+      return;
+    }
+  }
 #define SBSE_CALL(n) FastOps<T>::template fwd<n>(g, a, s)
   SBSE_FAST_SWITCH(g.N, SBSE_CALL)
 #undef SBSE_CALL
@@ -871,6 +880,11 @@ template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdAr
 template <typename T>
 void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_items, int mult, cudaStream_t s, int *tma_err) {
   if constexpr (sizeof(T) == 4) {
+    if (split_size(g.N)) {
+      launch_zcol2(g, d, n_items, mult, s);
+      count_launch(1);
+      return;
+    }
     if (tma_err) {
       bool done = false;
 #define SBSE_CALL(n) done = zcol_tma<n>(g, d, n_items, mult, tma_err, s)
@@ -892,6 +906,11 @@ template <typename T>
 void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items, const C2<T> *a_next, int L,
                           T *dens, cudaStream_t s, int *tma_err) {
   if constexpr (sizeof(T) == 4) {
+    if (split_size(g.N)) {
+      launch_plane_inv2_orb(g, d, n_items, a_next, L, dens, s);
+      count_launch(1);
+      return;
+    }
     if (dens && tma_err) {
       bool done = false;
 #define SBSE_CALL(n) done = inv_density_tma<n>(g, d, n_items, a_next, L, dens, tma_err, s)
@@ -914,6 +933,13 @@ void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items, const C
 template <typename T>
 void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots, const PoissonOut &po,
                               T *u_out, T *acc, C2<T> *em1_out, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (split_size(g.N)) {
+      launch_plane_inv2_poisson(g, d, n_slots, po, u_out, acc, em1_out, s);
+      count_launch(1);
+      return;
+    }
+  }
 #define SBSE_CALL(n) FastOps<T>::template inv<n>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, em1_out, po, PI_POISSON, s)
   SBSE_FAST_SWITCH(g.N, SBSE_CALL)
 #undef SBSE_CALL

@@ -1,7 +1,9 @@
 // Register-resident FFT of one pencil of compile-time length N (one thread per pencil).
 // Mixed-radix Stockham stages (radices 4, then 2, 3, 5) fully unrolled, so every index and every
 // twiddle index is a compile-time constant; the twiddles exp(-2 pi i k / N) are read from a
-// __constant__ table that the host fills from FP64 cos/sin.
+// __constant__ table that the host fills from FP64 cos/sin. The table is reached through a
+// provider type TW (static get(i) returning entry i of the layout below), so that every
+// translation unit can keep its own copy of the table.
 #pragma once
 
 #include "common.cuh"
@@ -9,7 +11,7 @@
 namespace sbse {
 
 // Sizes with a register FFT, and the offset of each size's twiddle table.
-constexpr int kRegSizes[] = {8, 10, 12, 16, 20, 24, 32, 40, 48, 64};
+constexpr int kRegSizes[] = {8, 10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96};
 constexpr int kRegCount = sizeof(kRegSizes) / sizeof(int);
 constexpr int reg_offset(int N) {
   int o = 0;
@@ -19,7 +21,7 @@ constexpr int reg_offset(int N) {
   }
   return -1;
 }
-constexpr int kRegTotal = reg_offset(64) + 64;
+constexpr int kRegTotal = reg_offset(96) + 96;
 
 constexpr int stage_radix(int N, int st) {
   int m = N, s = 0;
@@ -48,7 +50,7 @@ constexpr int stage_radix(int N, int st) {
 
 template <typename T> struct TwTab;
 
-template <typename T, int R, int SIGN>
+template <typename T, int R, int SIGN, typename TW = TwTab<T>>
 __device__ __forceinline__ void dft_small(C2<T> (&x)[R], int off, int N) {
   using C = C2<T>;
   if constexpr (R == 2) {
@@ -63,7 +65,7 @@ __device__ __forceinline__ void dft_small(C2<T> (&x)[R], int off, int N) {
     x[1] = cadd(d02, d13);
     x[3] = csub(d02, d13);
   } else if constexpr (R == 3) {
-    const T s3 = -TwTab<T>::get(off + N / 3).y;
+    const T s3 = -TW::get(off + N / 3).y;
     C t = cadd(x[1], x[2]);
     C m = C{x[0].x - T(0.5) * t.x, x[0].y - T(0.5) * t.y};
     C d = cmul_si(cscale(csub(x[1], x[2]), s3), SIGN);
@@ -71,7 +73,7 @@ __device__ __forceinline__ void dft_small(C2<T> (&x)[R], int off, int N) {
     x[1] = cadd(m, d);
     x[2] = csub(m, d);
   } else {  // R == 5
-    const C w1 = TwTab<T>::get(off + N / 5), w2 = TwTab<T>::get(off + 2 * (N / 5));
+    const C w1 = TW::get(off + N / 5), w2 = TW::get(off + 2 * (N / 5));
     const T c1 = w1.x, s1 = -w1.y, c2 = w2.x, s2 = -w2.y;
     C a1 = cadd(x[1], x[4]), a2 = cadd(x[2], x[3]);
     C b1 = csub(x[1], x[4]), b2 = csub(x[2], x[3]);
@@ -87,7 +89,7 @@ __device__ __forceinline__ void dft_small(C2<T> (&x)[R], int off, int N) {
   }
 }
 
-template <typename T, int N, int SIGN, int ST, int NS> struct RegStage {
+template <typename T, int N, int SIGN, int ST, int NS, typename TW> struct RegStage {
   __device__ __forceinline__ static void run(C2<T> (&v)[N]) {
     constexpr int R = stage_radix(N, ST);
     if constexpr (R != 0) {
@@ -103,27 +105,28 @@ template <typename T, int N, int SIGN, int ST, int NS> struct RegStage {
         for (int r = 0; r < R; ++r) {
           x[r] = v[j + r * nb];
           if (r > 0 && jm != 0) {
-            C2<T> t = TwTab<T>::get(off + (r * jm * tstride) % N);
+            C2<T> t = TW::get(off + (r * jm * tstride) % N);
             if (SIGN > 0) t.y = -t.y;
             x[r] = cmul(x[r], t);
           }
         }
-        dft_small<T, R, SIGN>(x, off, N);
+        dft_small<T, R, SIGN, TW>(x, off, N);
         const int idxD = (j / NS) * NS * R + jm;
 #pragma unroll
         for (int r = 0; r < R; ++r) w[idxD + r * NS] = x[r];
       }
 #pragma unroll
       for (int i = 0; i < N; ++i) v[i] = w[i];
-      RegStage<T, N, SIGN, ST + 1, NS * R>::run(v);
+      RegStage<T, N, SIGN, ST + 1, NS * R, TW>::run(v);
     }
   }
 };
 
 // In-register FFT of v (natural order in, natural order out). SIGN = -1 forward, +1 inverse
 // (unnormalised).
-template <typename T, int N, int SIGN> __device__ __forceinline__ void fft_reg(C2<T> (&v)[N]) {
-  RegStage<T, N, SIGN, 0, 1>::run(v);
+template <typename T, int N, int SIGN, typename TW = TwTab<T>>
+__device__ __forceinline__ void fft_reg(C2<T> (&v)[N]) {
+  RegStage<T, N, SIGN, 0, 1, TW>::run(v);
 }
 
 }  // namespace sbse

@@ -1,0 +1,461 @@
+// Three-pass 3D FFT round trip for the grid edges N = 80 and 96 (FP32): the split-operator step
+// of Eq. (10), the Poisson solves of Eq. (11) / q_ij and the exchange potentials of Eq. (1) on the
+// paper-scale grids (the 520-electron system of Sec. III sits on ~0.85M points, 96^3 here).
+//
+// A pencil of N points is too long for one thread's registers next to the epilogue's state, so it
+// is split over a lane pair (l, l ^ 16) of one warp: N = 2H, each lane holds H points, transforms
+// them with the register FFT of length H, and one radix-2 butterfly across the pair (operands
+// swapped by warp shuffles) completes the transform. Forward transforms take the pencil
+// interleaved (lane s holds x[2m + s]) and return it in two quarter blocks (decimation in time);
+// inverse transforms take the blocks and return the interleaved order (decimation in frequency),
+// so no pass needs a reordering step. A warp transforms 16 pencils; 16 consecutive lanes always
+// touch 16 consecutive grid points or rows of a padded shared-memory tile (conflict-free, 128-byte
+// global segments).
+//
+//   plane forward : one z-plane per block (2N threads): fused pre-operation, x FFTs in the padded
+//                   tile, y FFTs stored to global
+//   z columns     : 16 columns per warp: forward z FFT, kinetic propagator or 4 pi / |G|^2 (with
+//                   1/N^3), inverse z FFT
+//   plane inverse : y then x inverse FFTs of one z-plane; plain store, store plus the induced density
+//                   of the pair's L orbitals (Eq. 11), or the Poisson unpacking with the damped
+//                   time-integral accumulation of Eq. (13)
+// Blocks are ordered plane-major (plane outer, item inner), so the tables read beside the orbitals
+// (eta0 of each stochastic orbital, the potential phases, E - 1 of each pair) are the same z-slice
+// for consecutive blocks and stay in L2 even when the whole table set does not fit there.
+#include <math.h>
+
+#include "fft_reg.cuh"
+#include "kernels.h"
+#include "passes.cuh"
+
+namespace sbse {
+
+namespace {
+
+__constant__ float2 c_tws[kRegTotal];
+
+struct TwS {
+  __device__ __forceinline__ static float2 get(int i) { return c_tws[i]; }
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// exp(SIGN 2 pi i k / N)
+template <int N, int SIGN> __device__ __forceinline__ float2 tw_full(int k) {
+  float2 w = TwS::get(reg_offset(N) + k);
+  if (SIGN > 0) w.y = -w.y;
+  return w;
+}
+
+__device__ __forceinline__ float2 shfl_pair(float2 v) {
+  return make_float2(__shfl_xor_sync(kFull, v.x, 16), __shfl_xor_sync(kFull, v.y, 16));
+}
+
+// Decimation in time across the lane pair. On entry lane s of the pair holds x[2m + s], m < H;
+// on return it holds X[s Q + j] in v[j] and X[H + s Q + j] in v[Q + j] (j < Q = H / 2), where
+// X[k] = sum_n x[n] exp(SIGN 2 pi i n k / N): X[k] = E[k] + W^k O[k], X[k + H] = E[k] - W^k O[k]
+// with E, O the H-point transforms of the even and odd samples.
+template <int N, int SIGN> __device__ __forceinline__ void fft2_dit(float2 (&v)[N / 2], int s) {
+  constexpr int H = N / 2, Q = H / 2;
+  fft_reg<float, H, SIGN, TwS>(v);
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    // lane 0 keeps E[j] and needs O[j]; lane 1 keeps O[Q + j] and needs E[Q + j]
+    const float2 rcv = shfl_pair(s ? v[j] : v[Q + j]);
+    const float2 e = s ? rcv : v[j];
+    const float2 o = s ? v[Q + j] : rcv;
+    float2 t = cmul(o, tw_full<N, SIGN>(j));
+    if (s) t = cmul_si(t, SIGN);  // W^Q = exp(SIGN i pi / 2) = SIGN i
+    v[j] = cadd(e, t);
+    v[Q + j] = csub(e, t);
+  }
+}
+
+// Decimation in frequency across the lane pair: the inverse of the layout change above. On entry
+// lane s holds X[s Q + j] in v[j] and X[H + s Q + j] in v[Q + j]; on return it holds x[2m + s] in
+// v[m], x[n] = sum_k X[k] exp(SIGN 2 pi i n k / N). The even outputs are the H-point transform of
+// a_k = X[k] + X[k + H], the odd ones that of b_k = (X[k] - X[k + H]) W^k; lane 0 gathers every
+// a_k and lane 1 every b_k.
+template <int N, int SIGN> __device__ __forceinline__ void fft2_dif(float2 (&v)[N / 2], int s) {
+  constexpr int H = N / 2, Q = H / 2;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    const float2 a = cadd(v[j], v[Q + j]);
+    float2 b = cmul(csub(v[j], v[Q + j]), tw_full<N, SIGN>(j));
+    if (s) b = cmul_si(b, SIGN);
+    const float2 rcv = shfl_pair(s ? a : b);
+    v[j] = s ? rcv : a;
+    v[Q + j] = s ? b : rcv;
+  }
+  fft_reg<float, H, SIGN, TwS>(v);
+}
+
+// the padded plane tile; the density pass adds the pair's density accumulator (N^2 floats)
+template <int N> constexpr size_t split_smem() { return (size_t)N * (N + 1) * sizeof(float2); }
+template <int N> constexpr size_t split_density_smem() { return split_smem<N>() + (size_t)N * N * sizeof(float); }
+
+// ------------------------------------------------------------------------------------------
+// plane forward pass: block = (plane z, item), 2N threads
+
+template <int N, bool PAIR>
+__global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<float> g, XfwdArgs<float> a, int n_items) {
+  using C = float2;
+  constexpr int LD = N + 1, NN = N * N, NT = 2 * N, H = N / 2, Q = H / 2, KP = NN / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  const int z = (int)(blockIdx.x / (unsigned)n_items);
+  const long long item = (long long)blockIdx.x - (long long)z * n_items;
+  const long long off = (long long)z * NN;
+  const PreopItem<float> it = preop_item<float>(g, a, item);
+  constexpr int UB = 8;
+  if constexpr (PAIR) {
+    const C *dp = it.in + off, *ap = it.a + off, *pp = it.pv + off;
+    const C *ep = it.em1 ? it.em1 + off : nullptr;
+#pragma unroll 1
+    for (int k0 = 0; k0 < KP; k0 += UB) {
+      C dv[UB], av[UB], pv[UB], ev[UB];
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k0 + k < KP) {
+          const int l = threadIdx.x + (k0 + k) * NT;
+          dv[k] = dp[l];
+          av[k] = ap[l];
+          pv[k] = pp[l];
+          ev[k] = ep ? ep[l] : C{0.f, 0.f};
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k0 + k < KP) {
+          const int l = threadIdx.x + (k0 + k) * NT;
+          const int y = l / N, x = l - y * N;
+          S[y * LD + x] = pair_phase<float>(pv[k], ev[k], av[k], renorm_value<float>(dv[k], av[k], it.cm1));
+        }
+      }
+    }
+  } else {
+    auto run = [&](auto f) {
+#pragma unroll 1
+      for (int k0 = 0; k0 < KP; k0 += UB) {
+        C v[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k)
+          if (k0 + k < KP) v[k] = f(off + threadIdx.x + (k0 + k) * NT);
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          if (k0 + k < KP) {
+            const int l = threadIdx.x + (k0 + k) * NT;
+            const int y = l / N, x = l - y * N;
+            S[y * LD + x] = v[k];
+          }
+        }
+      }
+    };
+    if (it.mode == XF_PHASE_A) {
+      run([&](long long i) { return cmul(it.pv[i], it.in[i]); });
+    } else if (it.mode == XF_PACK_DN) {
+      if (it.r1)
+        run([&](long long i) { return C{it.r0[i], it.r1[i]}; });
+      else
+        run([&](long long i) { return C{it.r0[i], 0.f}; });
+    } else if (it.mode == XF_PACK_PROD) {
+      if (it.r2)
+        run([&](long long i) { return C{it.r0[i] * it.r1[i], it.r2[i] * it.r3[i]}; });
+      else
+        run([&](long long i) { return C{it.r0[i] * it.r1[i], 0.f}; });
+    } else {
+      run([&](long long i) { return preop_at<float>(g, it, i); });
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
+  {  // x transforms, pencil p = row p of the tile, in place
+    C v[H];
+    C *row = S + p * LD;
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = row[2 * m + s];
+    fft2_dit<N, -1>(v, s);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      row[s * Q + j] = v[j];
+      row[H + s * Q + j] = v[Q + j];
+    }
+  }
+  __syncthreads();
+  {  // y transforms, pencil p = column p, stored to global
+    C v[H];
+    const C *col = S + p;
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = col[(2 * m + s) * LD];
+    fft2_dit<N, -1>(v, s);
+    C *out = a.out + item * g.ng + off + p;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      out[(s * Q + j) * N] = v[j];
+      out[(H + s * Q + j) * N] = v[Q + j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// z columns: 64 columns per block of 128 threads (NN is a multiple of 64 for N = 80, 96)
+
+template <int N>
+__global__ void __launch_bounds__(128) k_zcol2(GView<float> g, float2 *data, int mult) {
+  using C = float2;
+  constexpr int NN = N * N, H = N / 2, Q = H / 2;
+  const int lane = threadIdx.x & 31, s = lane >> 4;
+  const long long c = (long long)blockIdx.x * 64 + (threadIdx.x >> 5) * 16 + (lane & 15);
+  const long long item = c / NN;
+  const int rem = (int)(c - item * NN), y = rem / N, x = rem - y * N;
+  C *base = data + item * g.ng + rem;
+  C v[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) v[m] = base[(long long)(2 * m + s) * NN];
+  fft2_dit<N, -1>(v, s);
+  const float inv_ng = 1.f / (float)(N * N * N);
+  if (mult == Z_KINETIC) {
+    const C mxy = cscale(cmul(g.kin[x], g.kin[y]), inv_ng);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      v[j] = cmul(v[j], cmul(mxy, g.kin[s * Q + j]));
+      v[Q + j] = cmul(v[Q + j], cmul(mxy, g.kin[H + s * Q + j]));
+    }
+  } else {
+    const float gxy = g.k2[x] + g.k2[y];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float G2 = gxy + g.k2[h * H + s * Q + j];
+        v[h * Q + j] = cscale(v[h * Q + j], G2 > 0.f ? float(4.0 * M_PI) * inv_ng / G2 : 0.f);
+      }
+    }
+  }
+  fft2_dif<N, +1>(v, s);
+#pragma unroll
+  for (int m = 0; m < H; ++m) base[(long long)(2 * m + s) * NN] = v[m];
+}
+
+// ------------------------------------------------------------------------------------------
+// plane inverse pass: block = (plane z, unit), unit = pair (DENSITY) or item (PLAIN, POISSON)
+
+enum { SP_PLAIN = 0, SP_DENSITY = 1, SP_POISSON = 2 };
+
+// y inverse FFTs of plane z of `src` (global, frequency blocks) into the tile (interleaved rows),
+// then x inverse FFTs in the tile; ends with the tile complete
+template <int N>
+__device__ __forceinline__ void inverse_plane2(float2 *S, const float2 *src, int s, int p) {
+  using C = float2;
+  constexpr int LD = N + 1, H = N / 2, Q = H / 2;
+  {
+    C v[H];
+    const C *col = src + p;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      v[j] = col[(s * Q + j) * N];
+      v[Q + j] = col[(H + s * Q + j) * N];
+    }
+    fft2_dif<N, +1>(v, s);
+#pragma unroll
+    for (int m = 0; m < H; ++m) S[(2 * m + s) * LD + p] = v[m];
+  }
+  __syncthreads();
+  {
+    C v[H];
+    C *row = S + p * LD;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      v[j] = row[s * Q + j];
+      v[Q + j] = row[H + s * Q + j];
+    }
+    fft2_dif<N, +1>(v, s);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < H; ++m) row[2 * m + s] = v[m];
+  }
+  __syncthreads();
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(2 * N, (MODE == SP_DENSITY || N == 96) ? 2 : 3) k_plane_inv2(GView<float> g, float2 *data, const float2 *a_next,
+                                                      float *dens, float *u_out, float *acc, float2 *em1_out,
+                                                      int n_units, int L, PoissonOut po) {
+  using C = float2;
+  constexpr int LD = N + 1, NN = N * N, NT = 2 * N, KP = NN / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  const int z = (int)(blockIdx.x / (unsigned)n_units);
+  const int unit = (int)blockIdx.x - z * n_units;
+  const long long off = (long long)z * NN;
+  const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
+  if constexpr (MODE == SP_DENSITY) {
+    // induced density 2 sum_l (2 Re(conj(eta0_l) d_l) + |d_l|^2) of the pair (Eq. 11), summed in
+    // shared memory behind the tile (registers hold the pencils)
+    float *D = reinterpret_cast<float *>(S + N * LD);
+    for (int ell = 0; ell < L; ++ell) {
+      const long long item = (long long)unit * L + ell;
+      C *base = data + item * g.ng + off;
+      inverse_plane2<N>(S, base, s, p);
+      const C *ab = a_next + (long long)ell * g.ng + off;
+      constexpr int UB = 8;
+#pragma unroll 1
+      for (int k0 = 0; k0 < KP; k0 += UB) {
+        C a0[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k)
+          if (k0 + k < KP) a0[k] = ab[threadIdx.x + (k0 + k) * NT];
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          if (k0 + k < KP) {
+            const int l = threadIdx.x + (k0 + k) * NT;
+            const int y = l / N, x = l - y * N;
+            const C dv = S[y * LD + x];
+            base[l] = dv;
+            const float t = 2.f * (2.f * (a0[k].x * dv.x + a0[k].y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+            D[l] = ell ? D[l] + t : t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    float *db = dens + (long long)unit * g.ng + off;
+#pragma unroll 4
+    for (int k = 0; k < KP; ++k) db[threadIdx.x + k * NT] = D[threadIdx.x + k * NT];
+  } else if constexpr (MODE == SP_PLAIN) {
+    C *base = data + (long long)unit * g.ng + off;
+    inverse_plane2<N>(S, base, s, p);
+#pragma unroll 4
+    for (int k = 0; k < KP; ++k) {
+      const int l = threadIdx.x + k * NT;
+      const int y = l / N, x = l - y * N;
+      base[l] = S[y * LD + x];
+    }
+  } else {
+    // Poisson epilogue: the two real potentials of the slot; u, the damped time integral, E - 1
+    const long long item = unit;
+    inverse_plane2<N>(S, data + item * g.ng + off, s, p);
+    const float coef = (float)po.coef, tau = (float)po.tau_next;
+    const bool keep = po.keep != 0.0;
+    const int n_h = (2 * item + 1 < po.n_out) ? 2 : 1;
+    constexpr int UB = 8;
+#pragma unroll 1
+    for (int k0 = 0; k0 < KP; k0 += UB) {
+      C v[UB];
+      float old[UB][2];
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k0 + k >= KP) break;
+        const int l = threadIdx.x + (k0 + k) * NT;
+        const int y = l / N, x = l - y * N;
+        v[k] = S[y * LD + x];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          old[k][h] = (acc && keep && h < n_h) ? acc[(2 * item + h) * g.ng + off + l] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k0 + k >= KP) break;
+        const int l = threadIdx.x + (k0 + k) * NT;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h >= n_h) break;
+          const float val = h ? v[k].y : v[k].x;
+          const long long o = (2 * item + h) * g.ng + off + l;
+          if (u_out) u_out[o] = val;
+          if (acc) acc[o] = old[k][h] + coef * val;
+          if (em1_out) em1_out[o] = phase_em1<float>(val, tau);
+        }
+      }
+    }
+  }
+}
+
+template <int N> void set_split_attrs() {
+  const int sm = (int)split_smem<N>();
+  cudaFuncSetAttribute(k_plane_fwd2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_fwd2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_inv2<N, SP_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_inv2<N, SP_DENSITY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)split_density_smem<N>());
+  cudaFuncSetAttribute(k_plane_inv2<N, SP_POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+template <int N> void fwd2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)a.n_items * N;
+  if (a.mode == XF_PHASE_PAIR)
+    k_plane_fwd2<N, true><<<blocks, 2 * N, split_smem<N>(), s>>>(view(g), a, a.n_items);
+  else
+    k_plane_fwd2<N, false><<<blocks, 2 * N, split_smem<N>(), s>>>(view(g), a, a.n_items);
+}
+
+template <int N> void zcol2(const GridTables<float> &g, float2 *d, int n_items, int mult, cudaStream_t s) {
+  static_assert((N * N) % 64 == 0, "z pass blocks hold 64 whole columns");
+  const unsigned blocks = (unsigned)((long long)n_items * N * N / 64);
+  k_zcol2<N><<<blocks, 128, 0, s>>>(view(g), d, mult);
+}
+
+template <int N>
+void inv2(const GridTables<float> &g, float2 *d, int n_units, const float2 *a_next, int L, float *dens,
+          float *u_out, float *acc, float2 *em1_out, const PoissonOut &po, int mode, cudaStream_t s) {
+  const unsigned blocks = (unsigned)n_units * N;
+  const size_t sm = split_smem<N>();
+  if (mode == SP_DENSITY)
+    k_plane_inv2<N, SP_DENSITY><<<blocks, 2 * N, split_density_smem<N>(), s>>>(view(g), d, a_next, dens, nullptr, nullptr, nullptr,
+                                                         n_units, L, po);
+  else if (mode == SP_PLAIN)
+    k_plane_inv2<N, SP_PLAIN><<<blocks, 2 * N, sm, s>>>(view(g), d, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                       n_units, 1, po);
+  else
+    k_plane_inv2<N, SP_POISSON><<<blocks, 2 * N, sm, s>>>(view(g), d, nullptr, nullptr, u_out, acc, em1_out,
+                                                         n_units, 1, po);
+}
+
+}  // namespace
+
+bool split_size(int N) { return N == 80 || N == 96; }
+
+int upload_split_twiddles() {
+  float2 hf[kRegTotal];
+  for (int s = 0; s < kRegCount; ++s) {
+    const int N = kRegSizes[s], off = reg_offset(N);
+    for (int k = 0; k < N; ++k) {
+      const double a = -2.0 * M_PI * (double)k / (double)N;
+      hf[off + k] = make_float2((float)cos(a), (float)sin(a));
+    }
+  }
+  return cudaMemcpyToSymbol(c_tws, hf, sizeof(hf)) == cudaSuccess ? 0 : -1;
+}
+
+void init_split_kernels() {
+  set_split_attrs<80>();
+  set_split_attrs<96>();
+}
+
+void launch_plane_fwd2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s) {
+  if (g.N == 80) fwd2<80>(g, a, s);
+  else if (g.N == 96) fwd2<96>(g, a, s);
+}
+
+void launch_zcol2(const GridTables<float> &g, float2 *d, int n_items, int mult, cudaStream_t s) {
+  if (g.N == 80) zcol2<80>(g, d, n_items, mult, s);
+  else if (g.N == 96) zcol2<96>(g, d, n_items, mult, s);
+}
+
+void launch_plane_inv2_orb(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L,
+                           float *dens, cudaStream_t s) {
+  const PoissonOut po{0, 0.0, 0.0, 0.0};
+  const int mode = dens ? SP_DENSITY : SP_PLAIN;
+  const int units = dens ? n_items / L : n_items;
+  if (g.N == 80) inv2<80>(g, d, units, a_next, L, dens, nullptr, nullptr, nullptr, po, mode, s);
+  else if (g.N == 96) inv2<96>(g, d, units, a_next, L, dens, nullptr, nullptr, nullptr, po, mode, s);
+}
+
+void launch_plane_inv2_poisson(const GridTables<float> &g, float2 *d, int n_slots, const PoissonOut &po,
+                               float *u_out, float *acc, float2 *em1_out, cudaStream_t s) {
+  if (g.N == 80) inv2<80>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, em1_out, po, SP_POISSON, s);
+  else if (g.N == 96) inv2<96>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, em1_out, po, SP_POISSON, s);
+}
+
+}  // namespace sbse

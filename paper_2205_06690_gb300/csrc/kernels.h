@@ -26,12 +26,18 @@ void count_launch(int n);
 
 // ---- register-pencil three-pass round trip (fft_fast.cu), for the sizes fast_supported<T>(N)
 int upload_reg_twiddles();
+// ---- lane-pair split-pencil passes for the grid edges 80 and 96, FP32 (fft_split.cu); the
+// launchers of fft_fast.cu route those sizes here
+bool split_size(int N);
+int upload_split_twiddles();
+void init_split_kernels();
 template <typename T> bool fast_supported(int N);
 template <typename T> void init_fast_kernels();
 template <typename T> struct XfwdArgs;
 template <typename T> struct GridTables;
 
 // ---- FFT passes (tdh_kernels.cu). Items are contiguous arrays of ng complex values.
+struct PoissonOut;
 enum XfwdMode { XF_PHASE_A = 0, XF_PHASE_PAIR = 1, XF_PACK_DN = 2, XF_PACK_PROD = 3 };
 
 template <typename T> struct XfwdArgs {
@@ -71,6 +77,12 @@ struct PoissonOut {
 template <typename T> void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots,
                                                     const PoissonOut &po, T *u_out, T *acc,
                                                     C2<T> *em1_out, cudaStream_t s);
+void launch_plane_fwd2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s);
+void launch_zcol2(const GridTables<float> &g, float2 *d, int n_items, int mult, cudaStream_t s);
+void launch_plane_inv2_orb(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L,
+                           float *dens, cudaStream_t s);
+void launch_plane_inv2_poisson(const GridTables<float> &g, float2 *d, int n_slots, const PoissonOut &po,
+                               float *u_out, float *acc, float2 *em1_out, cudaStream_t s);
 // out = exp(-i V_loc tau), computed in FP64 from the FP64 potential v64
 template <typename T> void launch_phase_table(const double *v64, long long ng, double tau, C2<T> *out,
                                               cudaStream_t s);

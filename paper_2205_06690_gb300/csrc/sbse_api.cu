@@ -500,7 +500,8 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   }
   C *acur = a0, *anext = a1;
   // persistent step kernel: dependency-ordered tile queue and completion counters
-  const bool persistent = ctx->persistent && fast_supported<T>(ctx->N);
+  // (the persistent step kernel exists for the thread-per-pencil sizes only, not for 80 and 96)
+  const bool persistent = ctx->persistent && fast_supported<T>(ctx->N) && !split_size(ctx->N);
   StepQueue sq{};
   int step_grid = 0;
   long long epoch = 0;
@@ -895,7 +896,8 @@ int sbse_create(sbse_ctx **out, int device, int precision) {
   sbse::init_fft_kernels();
   sbse::init_fast_kernels<float>();
   sbse::init_fast_kernels<double>();
-  if (sbse::upload_reg_twiddles() != 0) {
+  sbse::init_split_kernels();
+  if (sbse::upload_reg_twiddles() != 0 || sbse::upload_split_twiddles() != 0) {
     g_create_error = "upload of the FFT twiddle tables failed";
     sbse_destroy(c);
     return SBSE_ERR_CUDA;

@@ -11,8 +11,10 @@ that order, from numpy.random.default_rng(seed).
 
 The lowest N_occ + n_c eigenpairs of H0 are the orbitals phi_s (real, normalised so that
 sum_r phi_s(r)^2 dV = 1, sign fixed so the largest-magnitude entry is positive) and eigenvalues
-eps_s: by dense diagonalisation when n_g <= 4096, otherwise by preconditioned LOBPCG started from
-seeded random vectors, followed by a Rayleigh-Ritz rotation.
+eps_s: by dense diagonalisation when n_g <= 4096; on grids of edge 64 and more, when a CUDA device
+is present, by Chebyshev-filtered subspace iteration on that device (chfsi.py); otherwise by
+preconditioned LOBPCG started from seeded random vectors, followed by a Rayleigh-Ritz rotation.
+SBSE_EIGENSOLVER=lobpcg|chfsi forces the iterative solver.
 """
 from __future__ import annotations
 
@@ -180,11 +182,24 @@ class ModelSystem:
         return self.N ** 3
 
 
+def _use_chfsi(N: int) -> bool:
+    forced = os.environ.get("SBSE_EIGENSOLVER", "")
+    if forced:
+        return forced == "chfsi"
+    if N < 64:
+        return False
+    try:
+        import torch
+        return bool(torch.cuda.is_available())
+    except ImportError:
+        return False
+
+
 def _cache_path(p: Preset, n_states: int, tol: float):
     root = os.environ.get("SBSE_INPUT_CACHE")
     if not root:
         return None
-    key = f"{p.N}-{p.box}-{p.n_wells}-{p.seed}-{n_states}-{tol}"
+    key = f"{p.N}-{p.box}-{p.n_wells}-{p.seed}-{n_states}-{tol}-{'chfsi' if _use_chfsi(p.N) else 'lobpcg'}"
     return os.path.join(root, "sys_" + hashlib.sha1(key.encode()).hexdigest()[:16] + ".npz")
 
 
@@ -201,6 +216,9 @@ def make_system(p: Preset, n_states: int | None = None, tol: float = 1e-6) -> Mo
     if p.N ** 3 <= 4096:
         e, vec = np.linalg.eigh(_dense_h0(p.N, p.box, v))
         e, vec = e[:n_states], vec[:, :n_states]
+    elif _use_chfsi(p.N):
+        from . import chfsi
+        e, vec = chfsi.lowest_states(p.N, p.box, v, n_states, p.seed, tol)
     else:
         e, vec = _lobpcg_h0(p.N, p.box, v, n_states, p.seed, tol)
     idx = np.argmax(np.abs(vec), axis=0)
