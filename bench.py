@@ -1,11 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the stochastic-BSE hot path on GB300.
 
-One step = the whole hot path over one synthetic system: W_ij for all n_o(n_o+1)/2 occupied pairs
-by stochastic TDH (L = 10 stochastic orbitals, all time steps, cleaning, damped time integral),
-the exchange and direct contractions, the FP64 Tamm-Dancoff matrix A and its lowest excitons.
-Default workload: 48^3 grid (16 bohr box, 40 Gaussian wells, seed 1), N_occ = 60 (120 electrons),
-n_o = 8, n_c = 16 (36 pairs, A is 128 x 128), 1000 steps of dt = 0.05, gamma = 0.1, M = 10.
+Workload (default): the paper-scale system, a 96^3 grid (24 bohr box, 170 Gaussian wells, seed 2),
+N_occ = 260 (520 electrons), n_o = 16, n_c = 32 (136 pairs, A is 512 x 512), L = 10 stochastic
+orbitals, 2000 steps of dt = 0.05, gamma = 0.1, cleaning every M = 10 steps.
+
+One step = W_ij for one block of pairs by stochastic TDH (all time steps, cleaning, damped time
+integral; the blocks of 17 pairs are taken in turn, so eight steps renew all 136), then the
+exchange and direct contractions over all pairs' W, the FP64 Tamm-Dancoff matrix A and its lowest
+excitons. The whole system is also run end to end through the C ABI from pinned host buffers.
+Smaller workloads (--workload mid48 / tiny16) advance all their pairs in every step.
 
 Metric: W-applications per second (pairs completed per second of device time) for the whole job.
 
@@ -37,7 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid48")
+    ap.add_argument("--workload", default="large96")
+    ap.add_argument("--pairs-per-step", type=int, default=None,
+                    help="pairs per benchmark step (default: all up to 64, else one eighth)")
+    ap.add_argument("--prof-steps", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--n-steps", type=int, default=None, help="override the TDH step count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -45,12 +52,23 @@ def parse():
     ap.add_argument("--chunk-mb", type=int, default=None, help="SBSE_OPT_CHUNK_MB (L2 chunking)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the whole-system end-to-end call "
+                    "(profiling runs); the pairs outside the timed blocks then keep W = 0")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------------------------------------
-# the oracle as the CPU baseline / reference arm (runs in a single-threaded child process)
+# the oracle as the CPU baseline / reference arm: one pair per host core, each in its own
+# single-threaded child process (pairs are independent W applications)
+
+class _StepClock(list):
+    """Passed to the oracle as its `record` list: time stamps of every accumulated sample u_n, i.e.
+    the end of each TDH step of its own loop (the oracle itself is unchanged)."""
+
+    def append(self, item):
+        super().append(time.perf_counter())
+
 
 def _oracle_child(spec_path: str) -> None:
     import numpy as np
@@ -66,40 +84,60 @@ def _oracle_child(spec_path: str) -> None:
     op = tdh.TDHParams(n_steps=spec["sample_steps"], dt=spec["dt"], gamma=spec["gamma"],
                        alpha=spec["alpha"], clean_every=spec["clean_every"])
     phi_o = phi[n_occ - n_o:n_occ]
-    i, j = n_o - 2, n_o - 1
+    i, j = spec["pair"]
     rho = phi_o[i] * phi_o[j]
-    times = []
-    for _ in range(spec["repeats"]):
-        t0 = time.perf_counter()
-        tdh.coulomb_periodic(rho, g) + tdh.tdh_w_pol(g, v, phi[:n_occ], rho, coeff, op)
-        times.append(time.perf_counter() - t0)
-    print(json.dumps({"times": times}))
+    clock = _StepClock()
+    t0 = time.perf_counter()
+    tdh.coulomb_periodic(rho, g) + tdh.tdh_w_pol(g, v, phi[:n_occ], rho, coeff, op, record=clock)
+    t1 = time.perf_counter()
+    # clock[n] = end of step n - 1 (clock[0]: after the set-up and the first cleaning)
+    print(json.dumps({"total": t1 - t0, "setup": clock[0] - t0,
+                      "steps": [b - a for a, b in zip(clock[:-1], clock[1:])]}))
 
 
-def run_oracle_sample(system, preset, n_steps, sample_steps, repeats, seed):
-    """Time the oracle on one pair for `sample_steps` TDH steps, single-threaded, in a child."""
+def oracle_cores() -> int:
+    """Host cores for the oracle children, bounded by the memory each needs."""
+    n = os.cpu_count() or 1
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = None
+    return max(1, min(n, 64) if avail is None else min(n, 64, int(avail // (6 << 30)) or 1))
+
+
+def run_oracle_parallel(system, preset, sample_steps, seed, cores=None):
+    """Run the oracle on `cores` pairs at once (one child each) for `sample_steps` TDH steps.
+    Returns (cores, per-child step times [list of lists], per-child set-up seconds)."""
     import numpy as np
+    cores = cores or oracle_cores()
+    pairs = [(i, j) for i in range(preset.n_o) for j in range(i, preset.n_o)]
     with tempfile.TemporaryDirectory() as td:
         sp = os.path.join(td, "sys.npz")
         np.savez(sp, phi=system.phi[:preset.n_occ], v_loc=system.v_loc)
-        spec = dict(system=sp, N=system.N, box=system.box, n_occ=preset.n_occ, n_o=preset.n_o,
-                    n_s=preset.n_s, dt=preset.dt, gamma=preset.gamma, alpha=preset.alpha,
-                    clean_every=preset.clean_every, sample_steps=sample_steps, repeats=repeats,
-                    seed=seed)
-        jp = os.path.join(td, "spec.json")
-        with open(jp, "w") as f:
-            json.dump(spec, f)
         env = dict(os.environ)
         for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             env[k] = "1"
-        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", jp],
-                           capture_output=True, text=True, env=env, cwd=ROOT)
-        if r.returncode != 0:
-            raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
-        times = json.loads(r.stdout.strip().splitlines()[-1])["times"]
-    # W-applications per second: one pair needs n_steps / sample_steps samples of this length
-    per_w = [t * n_steps / sample_steps for t in times]
-    return times, per_w
+        procs = []
+        for c in range(cores):
+            spec = dict(system=sp, N=system.N, box=system.box, n_occ=preset.n_occ, n_o=preset.n_o,
+                        n_s=preset.n_s, dt=preset.dt, gamma=preset.gamma, alpha=preset.alpha,
+                        clean_every=preset.clean_every, sample_steps=sample_steps, seed=seed,
+                        pair=pairs[(len(pairs) - 1 - c) % len(pairs)])
+            jp = os.path.join(td, f"spec{c}.json")
+            with open(jp, "w") as f:
+                json.dump(spec, f)
+            procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-child", jp],
+                                          stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                                          env=env, cwd=ROOT))
+        steps, setup = [], []
+        for pr in procs:
+            out, err = pr.communicate()
+            if pr.returncode != 0:
+                raise RuntimeError("oracle child failed: " + err[-2000:])
+            d = json.loads(out.strip().splitlines()[-1])
+            steps.append(d["steps"])
+            setup.append(d["setup"])
+    return cores, steps, setup
 
 
 def cpu_model() -> str:
@@ -165,7 +203,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_SOURCES = ["fft_fast.cu", "fft_reg.cuh", "passes.cuh", "tma.cuh", "common.cuh", "kernels.h"]
+KERNEL_SOURCES = ["fft_fast.cu", "fft_split.cu", "fft_reg.cuh", "passes.cuh", "tma.cuh", "common.cuh", "kernels.h"]
 
 
 def kernel_source_hash() -> str:
@@ -201,6 +239,13 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def block_default(pre) -> int:
+    """Pairs per benchmark step: every pair for the small workloads; one eighth of the 136 pairs of
+    the 96^3 system (17), so that one step (17 pairs x 2000 TDH steps + A + excitons) takes seconds
+    and eight steps refresh all of W."""
+    return pre.n_pairs if pre.n_pairs <= 64 else -(-pre.n_pairs // 8)
+
+
 def main():
     args = parse()
     if args.oracle_child:
@@ -216,30 +261,42 @@ def main():
     pre = si.preset(args.workload)
     n_steps = args.n_steps or pre.n_steps
     P = pre.n_pairs
+    pairs = [(i, j) for i in range(pre.n_o) for j in range(i, pre.n_o)]
+    blk = args.pairs_per_step or block_default(pre)
+    blocks = [pairs[b:b + blk] for b in range(0, P, blk)]
     workload = (f"{pre.name}: {pre.N}^3 grid, box {pre.box} bohr, {pre.n_wells} Gaussian wells "
                 f"(seed {pre.seed}), N_occ={pre.n_occ} ({2 * pre.n_occ} electrons), n_o={pre.n_o}, "
                 f"n_c={pre.n_c}, {P} pairs, L={pre.n_s}, {n_steps} steps dt={pre.dt}, "
                 f"gamma={pre.gamma}, M={pre.clean_every}, A {pre.n_o * pre.n_c}^2, "
                 f"{pre.n_exc} excitons")
+    step_def = (f"one step = W for one block of {blk} of the {P} pairs (all {n_steps} TDH steps, "
+                f"L={pre.n_s}; blocks in turn), then A from all {P} pairs' W and the lowest "
+                f"{pre.n_exc} excitons")
+    metric = "W-rho applications/sec (stochastic TDH, all pairs) + A build"
 
     if args.impl == "reference":
         if rank != 0:
             return
         system = si.make_system(pre)
-        sample = 20
-        times, per_w = run_oracle_sample(system, pre, n_steps, sample, args.warmup + args.steps,
-                                         seed=pre.seed)
-        timed = per_w[args.warmup:]
-        val = 1.0 / statistics.mean(timed)
+        k_steps = args.warmup + args.steps
+        cores, steps, setup = run_oracle_parallel(system, pre, k_steps, pre.seed)
+        # step k of the line = TDH step k of every child (each child one pair); the first W are
+        # the warm-up; W-applications/s = cores / (mean time of one TDH step x n_steps)
+        per = [statistics.mean(st[k] for st in steps) for k in range(k_steps)]
+        timed = per[args.warmup:]
+        val = cores / (statistics.mean(timed) * n_steps)
         line = {
-            "impl": "reference", "metric": "W-rho applications/sec (stochastic TDH, all pairs) + A build",
-            "value": val, "unit": "W-applications/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times[args.warmup:]),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload, "precision": "fp64 oracle"},
-            "cpu_baseline": {"value": val, "unit": "W-applications/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one pair x {sample} TDH steps per step, scaled to "
-                                       f"{n_steps} steps; host {cpu_model()}"},
+            "impl": "reference", "metric": metric, "value": val, "unit": "W-applications/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(timed), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "precision": "fp64 oracle",
+                       "step": f"one TDH step of one pair on each of {cores} host cores"},
+            "cpu_baseline": {"value": val, "unit": "W-applications/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} pairs at once (one single-threaded process each) x "
+                                       f"{k_steps} TDH steps; per-step times from the oracle's own loop, "
+                                       f"scaled to {n_steps} steps; set-up "
+                                       f"{statistics.mean(setup):.1f} s excluded; host {cpu_model()}"},
             "e2e": {"value": val, "unit": "W-applications/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
         }
@@ -249,11 +306,15 @@ def main():
     system = si.make_system(pre)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = 20
-        times, per_w = run_oracle_sample(system, pre, n_steps, sample, 2, seed=pre.seed)
-        cpu = {"value": 1.0 / min(per_w), "unit": "W-applications/s", "cores": 1, "kind": "oracle",
-               "sample": f"one pair of {pre.name} x {sample} TDH steps (best of 2, "
-                         f"{min(times):.1f} s), scaled to {n_steps} steps; host {cpu_model()}"}
+        sample = min(10, n_steps)
+        cores, steps, setup = run_oracle_parallel(system, pre, sample, pre.seed)
+        per_step = statistics.mean(statistics.mean(st) for st in steps)
+        cpu = {"value": cores / (per_step * n_steps), "unit": "W-applications/s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"{cores} pairs of {pre.name} at once (one single-threaded process each) x "
+                         f"{sample} TDH steps (mean step {per_step:.2f} s, set-up "
+                         f"{statistics.mean(setup):.1f} s excluded), scaled to {n_steps} steps; "
+                         f"host {cpu_model()}"}
 
     import torch
     torch.cuda.set_device(local)
@@ -263,11 +324,9 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     from paper_2205_06690_gb300 import binding as B
 
-    pairs = [(i, j) for i in range(pre.n_o) for j in range(i, pre.n_o)]
     prec = B.SBSE_MIXED if args.precision == "mixed" else B.SBSE_FP64
     prm = B.TDHParams(n_s=pre.n_s, n_steps=n_steps, clean_every=pre.clean_every, dt=pre.dt,
                       gamma=pre.gamma, alpha=pre.alpha, seed=pre.seed + 1000 * rank)
-    n = pre.n_o * pre.n_c
     ns = pre.n_occ + pre.n_c
     phi = np.ascontiguousarray(system.phi[:ns])
     eps = np.ascontiguousarray(system.eps[:ns])
@@ -279,23 +338,59 @@ def main():
     ctx = B.Context(local, prec)
     if args.chunk_mb is not None:
         B.sbse_set_option(ctx.h, B.SBSE_OPT_CHUNK_MB, args.chunk_mb)
-    ctx.set_grid(pre.N, pre.box, system.v_loc)
-    ctx.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi, eps, pre.scissor)
     ext = torch.cuda.ExternalStream(B.sbse_get_stream(ctx.h), device=dev)
 
-    def step():
+    # end to end through the C ABI, the whole system in one call: pinned host inputs -> all pairs'
+    # W -> A -> excitons copied back to the host (the first such call also captures the graph of
+    # the time loop; a second, timed call replays it)
+    v_pin = torch.from_numpy(np.ascontiguousarray(system.v_loc)).pin_memory()
+    phi_pin = torch.from_numpy(phi).pin_memory()
+    eps_pin = torch.from_numpy(eps).pin_memory()
+
+    def full_system():
+        ctx.set_grid(pre.N, pre.box, v_pin.numpy())
+        ctx.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi_pin.numpy(), eps_pin.numpy(), pre.scissor)
         ctx.apply_W(prm, pairs)
+        ctx.build_A(copy_out=False)
+        return ctx.spectrum(pre.n_exc)
+
+    e2e_runs = 0 if args.no_e2e else (args.e2e_steps or 1)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_runs):
+        full_system()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_runs if e2e_runs else None
+    if not e2e_runs:
+        ctx.set_grid(pre.N, pre.box, system.v_loc)
+        ctx.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi, eps, pre.scissor)
+        B.sbse_set_W(ctx.h, pairs, np.zeros((P, pre.N ** 3)))
+    if world > 1 and e2e_s:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = system.v_loc.nbytes + phi.nbytes + eps.nbytes + pre.n_s * pre.n_occ * 8
+    d2h = pre.n_exc * 8
+
+    # the benchmark step: W for the next block of pairs, then A and the excitons (all pairs' W
+    # are resident from the call above)
+    cursor = [0]
+
+    def step():
+        ctx.apply_W(prm, blocks[cursor[0] % len(blocks)])
+        cursor[0] += 1
         ctx.build_A(copy_out=False)
         return ctx.spectrum(pre.n_exc)
 
     for _ in range(args.warmup):
         ev = step()
-    # timed region: inputs resident in HBM; the propagated orbitals (P L n_g complex) exceed L2
+    # timed region: inputs resident in HBM, default configuration (time loop replayed as a graph);
+    # the propagated orbitals (blk L n_g complex) exceed L2
     barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    B.sbse_profile(ctx.h, True)
     launches0 = B.sbse_kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -308,16 +403,29 @@ def main():
     clocks = clk.stop()
     launches = B.sbse_kernel_launches() - launches0
     ms = e0.elapsed_time(e1)
-    phase = {ph: B.sbse_phase_time(ctx.h, ph) for ph in range(8)}
-    B.sbse_profile(ctx.h, False)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     ms_step = ms / args.steps
-    value = world * P / (ms_step / 1e3)
+    value = world * blk / (ms_step / 1e3)
 
-    # A-build time (orbitals resident -> A in FP64), measured separately
+    # per-pass times: further steps with events around every pass (this disables the graph replay,
+    # so they run as direct launches; their step time is reported beside the headline's)
+    prof_steps = max(1, args.prof_steps)
+    B.sbse_profile(ctx.h, True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(ext)
+    for _ in range(prof_steps):
+        step()
+    p1.record(ext)
+    torch.cuda.synchronize()
+    ms_prof = p0.elapsed_time(p1)
+    phase = {ph: B.sbse_phase_time(ctx.h, ph) for ph in range(8)}
+    B.sbse_profile(ctx.h, False)
+
+    # A-build time (orbitals and W resident -> A in FP64), measured separately
     ta0 = torch.cuda.Event(enable_timing=True)
     ta1 = torch.cuda.Event(enable_timing=True)
     ta0.record(ext)
@@ -337,35 +445,49 @@ def main():
     absorption = {"ms": 1e3 * (time.perf_counter() - t_abs), "n_terms": n_terms, "n_omega": len(omega),
                   "broadening_ev": 0.08, "axis": "x", "peak_omega_ha": float(omega[int(np.argmax(sig_abs))])}
 
-    # the plain FP64 GPU path on the same workload (shortened propagation, scaled to n_steps):
-    # the comparator of the mixed path
+    # the plain FP64 GPU path on the same block of pairs (shortened propagation, scaled to
+    # n_steps): the comparator of the mixed path
     fp64 = None
     if prec == B.SBSE_MIXED and not args.no_fp64_compare:
-        short = max(20, n_steps // 10)
+        short = max(20, n_steps // 100)
         prm64 = B.TDHParams(n_s=pre.n_s, n_steps=short, clean_every=pre.clean_every, dt=pre.dt,
+                            gamma=pre.gamma, alpha=pre.alpha, seed=prm.seed)
+        prm32 = B.TDHParams(n_s=pre.n_s, n_steps=short, clean_every=pre.clean_every, dt=pre.dt,
                             gamma=pre.gamma, alpha=pre.alpha, seed=prm.seed)
         with B.Context(local, B.SBSE_FP64) as c64:
             c64.set_grid(pre.N, pre.box, system.v_loc)
             c64.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi, eps, pre.scissor)
-            c64.apply_W(prm64, pairs)
+            c64.apply_W(prm64, blocks[0])
             ext64 = torch.cuda.ExternalStream(B.sbse_get_stream(c64.h), device=dev)
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
             f0.record(ext64)
-            c64.apply_W(prm64, pairs)
+            c64.apply_W(prm64, blocks[0])
             f1.record(ext64)
             torch.cuda.synchronize()
             ms64 = f0.elapsed_time(f1) * n_steps / short
-            # A-build time of the FP64 path (FP64 CUDA-core contractions), A built once before
+            # the FP64 A build (FP64 CUDA-core contractions) on W held by the mixed context
+            w_all = B.sbse_get_W(ctx.h, pairs, pre.N ** 3)
+            B.sbse_set_W(c64.h, pairs, w_all)
             c64.build_A(copy_out=False)
             f0.record(ext64)
             c64.build_A(copy_out=False)
             f1.record(ext64)
             torch.cuda.synchronize()
             a64_ms = f0.elapsed_time(f1)
-        fp64 = {"value": P / (ms64 / 1e3), "unit": "W-applications/s",
-                "sample": f"all {P} pairs x {short} TDH steps, scaled to {n_steps}",
-                "mixed_speedup": (P / (ms_step / 1e3)) / (P / (ms64 / 1e3)),
+            del w_all
+        # the mixed path on the same shortened run, for a like-for-like ratio
+        ctx.apply_W(prm32, blocks[0])
+        f0.record(ext)
+        ctx.apply_W(prm32, blocks[0])
+        f1.record(ext)
+        torch.cuda.synchronize()
+        ms32 = f0.elapsed_time(f1) * n_steps / short
+        ctx.apply_W(prm, blocks[0])  # restore the block's full-length W
+        fp64 = {"value": len(blocks[0]) / (ms64 / 1e3), "unit": "W-applications/s",
+                "sample": f"{len(blocks[0])} pairs x {short} TDH steps, scaled to {n_steps}",
+                "mixed_same_sample": len(blocks[0]) / (ms32 / 1e3),
+                "mixed_speedup": ms64 / ms32,
                 "a_build_ms": a64_ms, "a_build_speedup_mixed": a64_ms / a_build_ms}
 
     # learned form: FNO surrogate of the workload's shape (64^3, width 32, 12 modes, 4 layers)
@@ -382,91 +504,83 @@ def main():
         t0 = time.perf_counter()
         for _ in range(3):
             net.forward(4, xs.data_ptr(), ys.data_ptr())
+        torch.cuda.synchronize()
         t_inf = (time.perf_counter() - t0) / 12
         t0 = time.perf_counter()
         for _ in range(3):
             net.train_step(4, xs.data_ptr(), ys.data_ptr(), 1e-4)
+        torch.cuda.synchronize()
         t_tr = (time.perf_counter() - t0) / 12
         net.close()
         surrogate = {"network": "FNO 64^3, width 32, 12 modes/axis, 4 Fourier layers, BF16 weights",
                      "infer_ms_per_pair": 1e3 * t_inf, "train_ms_per_pair": 1e3 * t_tr,
-                     "tdh_ms_per_pair": ms_step / P}
+                     "tdh_ms_per_pair_this_workload": ms_step / blk}
 
-    # end to end through the C ABI: pinned host inputs -> excitons on the host, every step
-    e2e_steps = args.e2e_steps or max(1, min(args.steps, 2))
-    v_pin = torch.from_numpy(np.ascontiguousarray(system.v_loc)).pin_memory()
-    phi_pin = torch.from_numpy(phi).pin_memory()
-    eps_pin = torch.from_numpy(eps).pin_memory()
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.set_grid(pre.N, pre.box, v_pin.numpy())
-        ctx.set_orbitals(pre.n_occ, pre.n_o, pre.n_c, phi_pin.numpy(), eps_pin.numpy(), pre.scissor)
-        ev_e2e = step()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    h2d = system.v_loc.nbytes + phi.nbytes + eps.nbytes + pre.n_s * pre.n_occ * 8
-    d2h = pre.n_exc * 8
-
-    # Roofline. Algorithmic unit: one read and one write of every complex value of the pair batch
-    # (P L n_g points, 16 B/point in FP32). Each of the three passes of a step (phases 5, 6, 7,
-    # timed by events on the library's stream inside the timed region) is one such sweep; the
-    # dominant kernel is the pass with the largest share. The whole step (phase 0) is reported
-    # against the same per-step figure, so its fraction shows the cost of three sweeps per step.
+    # Roofline. Algorithmic unit: one read and one write of every complex value of the propagated
+    # block (blk L n_g points, 16 B/point in FP32). Each of the three passes of a TDH step (phases
+    # 5, 6, 7, timed by events on the library's stream) is one such sweep; the dominant kernel is
+    # the pass with the largest share. The whole propagation step (phase 0) is reported against the
+    # same per-step figure, so its fraction shows the cost of three sweeps per step.
     peak, src = measured_peaks()
     csize = 8 if prec == B.SBSE_MIXED else 16
-    sweep_bytes = P * pre.n_s * pre.N ** 3 * 2 * csize
-    pass_names = {5: "forward plane pass k_plane_fwd (potential phase + x, y FFTs)",
-                  6: "z-column pass k_zcol_tma (z FFT, kinetic phase, inverse z FFT)",
-                  7: "inverse plane pass k_plane_inv_density_tma (y, x inverse FFTs + density)"}
+    sweep_bytes = blk * pre.n_s * pre.N ** 3 * 2 * csize
+    split = pre.N in (80, 96)
+    pass_names = {5: "forward plane pass " + ("k_plane_fwd2" if split else "k_plane_fwd") +
+                     " (potential phase + x, y FFTs)",
+                  6: "z-column pass " + ("k_zcol2" if split else "k_zcol_tma") +
+                     " (z FFT, kinetic phase, inverse z FFT)",
+                  7: "inverse plane pass " + ("k_plane_inv2" if split else "k_plane_inv_density_tma") +
+                     " (y, x inverse FFTs + density)"}
     passes = {}
     for ph, name in pass_names.items():
         t, nl = phase[ph]
         if nl:
             gbs = sweep_bytes / (t / nl / 1e3) / 1e9
             passes[str(ph)] = {"kernel": name, "avg_us": 1e3 * t / nl, "launches": nl,
-                               "achieved": gbs, "frac": gbs / peak, "share_of_step": t / ms}
+                               "achieved": gbs, "frac": gbs / peak, "share_of_step": t / ms_prof}
     dom = max(passes, key=lambda k: passes[k]["share_of_step"]) if passes else None
     traffic, traffic_note = profiled_traffic(dom and int(dom), pre.name, prec == B.SBSE_MIXED)
     ms0, n0 = phase[0]
     step_gbs = (sweep_bytes + pre.n_s * pre.N ** 3 * 2 * csize) / (ms0 / n0 / 1e3) / 1e9 if n0 else None
+    prof_note = (f"{prof_steps} further benchmark steps with CUDA events around every pass on the "
+                 f"library stream (direct launches, {ms_prof / prof_steps:.1f} ms per step vs "
+                 f"{ms_step:.1f} ms in the timed region with graph replay)")
     if dom:
         roofline = {"bound": "hbm", "achieved": passes[dom]["achieved"], "peak": peak, "unit": "GB/s",
                     "frac": passes[dom]["frac"], "traffic": traffic, "traffic_source": traffic_note,
                     "kernel": passes[dom]["kernel"], "bytes_per_launch": sweep_bytes,
                     "avg_launch_us": passes[dom]["avg_us"], "share_of_step": passes[dom]["share_of_step"],
-                    "peak_source": src, "passes": passes,
+                    "peak_source": src, "timing": prof_note, "passes": passes,
                     "step": {"achieved": step_gbs, "frac": step_gbs / peak if step_gbs else None,
-                             "share_of_step": ms0 / ms if ms else None}}
+                             "share_of_step": ms0 / ms_prof if ms_prof else None}}
     else:
         roofline = {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
                     "frac": step_gbs / peak if step_gbs else None, "traffic": None,
-                    "kernel": "propagation step", "peak_source": src}
+                    "kernel": "propagation step", "peak_source": src, "timing": prof_note}
     line = {
-        "metric": "W-rho applications/sec (stochastic TDH, all pairs) + A build",
+        "metric": metric,
         "value": value, "unit": "W-applications/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == B.SBSE_MIXED else "f64", "data": "synthetic",
-        "config": {"workload": workload,
-                   "precision": "mixed: FP32 FFT/propagation/cleaning, FP64 W accumulator, A, "
-                                "eigensolve" if prec == B.SBSE_MIXED else "fp64",
-                   "l2": "inputs larger than L2 (propagated orbitals "
-                         f"{P * pre.n_s * pre.N ** 3 * csize / 1e6:.0f} MB)",
+        "config": {"workload": workload, "step": step_def,
+                   "precision": "mixed: FP32 FFT/propagation, BF16-split tensor-core cleaning and "
+                                "contractions, FP64 W accumulator, A, eigensolve"
+                                if prec == B.SBSE_MIXED else "fp64",
+                   "l2": "inputs larger than L2 (propagated orbitals of one block "
+                         f"{blk * pre.n_s * pre.N ** 3 * csize / 1e6:.0f} MB)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": world * P / e2e_s, "unit": "W-applications/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "what": f"whole system per call: pinned host v_loc, orbitals, eps -> all {P} pairs' W "
+                        f"-> A -> excitons to the host ({e2e_s:.2f} s per call; the first call, so "
+                        f"it includes the capture of the time loop's graph)"} if e2e_s else None,
         "gpu_launches": launches,
         "roofline": roofline,
         "a_build_ms": a_build_ms,
         "absorption": absorption,
-        "phase_ms_per_step": {str(k): v[0] / args.steps for k, v in phase.items()},
+        "phase_ms_per_step": {str(k): v[0] / prof_steps for k, v in phase.items()},
         "excitons_ha": [float(x) for x in ev],
         "fp64_gpu_path": fp64,
         "surrogate": surrogate,
