@@ -91,6 +91,14 @@ template <int N, int SIGN> __device__ __forceinline__ void fft2_dif(float2 (&v)[
 }
 
 // the padded plane tile; the density pass adds the pair's density accumulator (N^2 floats)
+// 8-byte asynchronous global -> shared copy (cached in L1 only on the way, i.e. not at all reused)
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int N> constexpr size_t split_smem() { return (size_t)N * (N + 1) * sizeof(float2); }
 template <int N> constexpr size_t split_density_smem() { return split_smem<N>() + (size_t)N * N * sizeof(float); }
 
@@ -109,27 +117,39 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<flo
   const PreopItem<float> it = preop_item<float>(g, a, item);
   constexpr int UB = 8;
   if constexpr (PAIR) {
+    // the plane of d (the stream from HBM) goes into the tile by asynchronous copies, all at once;
+    // the tables beside it (eta0, the potential phase, E - 1) are the same z-slice for consecutive
+    // blocks and come from L2 in batches while the copies land
     const C *dp = it.in + off, *ap = it.a + off, *pp = it.pv + off;
     const C *ep = it.em1 ? it.em1 + off : nullptr;
+#pragma unroll 8
+    for (int k = 0; k < KP; ++k) {
+      const int l = threadIdx.x + k * NT;
+      const int y = l / N, x = l - y * N;
+      cp_async8(S + y * LD + x, dp + l);
+    }
+    cp_async_commit();
+    constexpr int UBP = 16;
 #pragma unroll 1
-    for (int k0 = 0; k0 < KP; k0 += UB) {
-      C dv[UB], av[UB], pv[UB], ev[UB];
+    for (int k0 = 0; k0 < KP; k0 += UBP) {
+      C av[UBP], pv[UBP], ev[UBP];
 #pragma unroll
-      for (int k = 0; k < UB; ++k) {
+      for (int k = 0; k < UBP; ++k) {
         if (k0 + k < KP) {
           const int l = threadIdx.x + (k0 + k) * NT;
-          dv[k] = dp[l];
           av[k] = ap[l];
           pv[k] = pp[l];
           ev[k] = ep ? ep[l] : C{0.f, 0.f};
         }
       }
+      if (k0 == 0) cp_async_wait_all();  // this thread's copies (it reads only those back)
 #pragma unroll
-      for (int k = 0; k < UB; ++k) {
+      for (int k = 0; k < UBP; ++k) {
         if (k0 + k < KP) {
           const int l = threadIdx.x + (k0 + k) * NT;
           const int y = l / N, x = l - y * N;
-          S[y * LD + x] = pair_phase<float>(pv[k], ev[k], av[k], renorm_value<float>(dv[k], av[k], it.cm1));
+          C *sp = S + y * LD + x;
+          *sp = pair_phase<float>(pv[k], ev[k], av[k], renorm_value<float>(*sp, av[k], it.cm1));
         }
       }
     }
@@ -202,7 +222,7 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<flo
 // z columns: 64 columns per block of 128 threads (NN is a multiple of 64 for N = 80, 96)
 
 template <int N>
-__global__ void __launch_bounds__(128) k_zcol2(GView<float> g, float2 *data, int mult) {
+__global__ void __launch_bounds__(128, 4) k_zcol2(GView<float> g, float2 *data, int mult) {
   using C = float2;
   constexpr int NN = N * N, H = N / 2, Q = H / 2;
   const int lane = threadIdx.x & 31, s = lane >> 4;
@@ -245,6 +265,8 @@ enum { SP_PLAIN = 0, SP_DENSITY = 1, SP_POISSON = 2 };
 
 // y inverse FFTs of plane z of `src` (global, frequency blocks) into the tile (interleaved rows),
 // then x inverse FFTs in the tile; ends with the tile complete
+// (the block barrier before the tile is written lets the column loads and y FFTs of this plane
+// overlap the previous use of the tile by other warps)
 template <int N>
 __device__ __forceinline__ void inverse_plane2(float2 *S, const float2 *src, int s, int p) {
   using C = float2;
@@ -258,6 +280,7 @@ __device__ __forceinline__ void inverse_plane2(float2 *S, const float2 *src, int
       v[Q + j] = col[(H + s * Q + j) * N];
     }
     fft2_dif<N, +1>(v, s);
+    __syncthreads();
 #pragma unroll
     for (int m = 0; m < H; ++m) S[(2 * m + s) * LD + p] = v[m];
   }
@@ -299,27 +322,21 @@ __global__ void __launch_bounds__(2 * N, (MODE == SP_DENSITY || N == 96) ? 2 : 3
       C *base = data + item * g.ng + off;
       inverse_plane2<N>(S, base, s, p);
       const C *ab = a_next + (long long)ell * g.ng + off;
-      constexpr int UB = 8;
-#pragma unroll 1
-      for (int k0 = 0; k0 < KP; k0 += UB) {
-        C a0[UB];
+      // every eta0 load of the epilogue in flight at once (the pencil registers are free here)
+      C a0[KP];
 #pragma unroll
-        for (int k = 0; k < UB; ++k)
-          if (k0 + k < KP) a0[k] = ab[threadIdx.x + (k0 + k) * NT];
+      for (int k = 0; k < KP; ++k) a0[k] = ab[threadIdx.x + k * NT];
 #pragma unroll
-        for (int k = 0; k < UB; ++k) {
-          if (k0 + k < KP) {
-            const int l = threadIdx.x + (k0 + k) * NT;
-            const int y = l / N, x = l - y * N;
-            const C dv = S[y * LD + x];
-            base[l] = dv;
-            const float t = 2.f * (2.f * (a0[k].x * dv.x + a0[k].y * dv.y) + dv.x * dv.x + dv.y * dv.y);
-            D[l] = ell ? D[l] + t : t;
-          }
-        }
+      for (int k = 0; k < KP; ++k) {
+        const int l = threadIdx.x + k * NT;
+        const int y = l / N, x = l - y * N;
+        const C dv = S[y * LD + x];
+        base[l] = dv;
+        const float t = 2.f * (2.f * (a0[k].x * dv.x + a0[k].y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+        D[l] = ell ? D[l] + t : t;
       }
-      __syncthreads();
     }
+    __syncthreads();
     float *db = dens + (long long)unit * g.ng + off;
 #pragma unroll 4
     for (int k = 0; k < KP; ++k) db[threadIdx.x + k * NT] = D[threadIdx.x + k * NT];

@@ -82,6 +82,7 @@ struct sbse_ctx {
   int use_graph = 1;
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned long long> graph_key;
+  long long graph_launches = 0;  // kernel launches recorded in graph_exec (counted on every replay)
   // bytes of propagated orbitals per chunk of pairs (SBSE_OPT_CHUNK_MB); 0 = all pairs at once
   double l2_chunk_bytes = 1e30;
   // profiling
@@ -676,6 +677,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   if (ctx->use_graph && !ctx->prof) {
     if (ctx->graph_exec && ctx->graph_key == key) {
       CK(cudaGraphLaunch(ctx->graph_exec, st));
+      count_launch((int)ctx->graph_launches);
       replayed = true;
     } else {
       if (ctx->graph_exec) {
@@ -684,7 +686,10 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       }
       cudaGraph_t graph = nullptr;
       if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        // launches issued while capturing are counted once here; they run in the replay below
+        const long long l0 = g_launches.load();
         const int rc_loop = time_loop();
+        ctx->graph_launches = g_launches.load() - l0;
         const cudaError_t e_end = cudaStreamEndCapture(st, &graph);
         if (rc_loop) {
           if (graph) cudaGraphDestroy(graph);
@@ -696,6 +701,8 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
           ctx->graph_key = key;
           CK(cudaGraphLaunch(exec, st));
           replayed = true;
+        } else {
+          count_launch(-(int)ctx->graph_launches);  // recorded, never run
         }
         if (graph) cudaGraphDestroy(graph);
       }
