@@ -906,11 +906,6 @@ template <typename T>
 void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items, const C2<T> *a_next, int L,
                           T *dens, cudaStream_t s, int *tma_err) {
   if constexpr (sizeof(T) == 4) {
-    if (split_size(g.N)) {
-      launch_plane_inv2_orb(g, d, n_items, a_next, L, dens, s);
-      count_launch(1);
-      return;
-    }
     if (dens && tma_err) {
       bool done = false;
 #define SBSE_CALL(n) done = inv_density_tma<n>(g, d, n_items, a_next, L, dens, tma_err, s)

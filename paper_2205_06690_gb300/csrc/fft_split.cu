@@ -12,13 +12,17 @@
 // touch 16 consecutive grid points or rows of a padded shared-memory tile (conflict-free, 128-byte
 // global segments).
 //
-//   plane forward : one z-plane per block (2N threads): fused pre-operation, x FFTs in the padded
-//                   tile, y FFTs stored to global
-//   z columns     : 16 columns per warp: forward z FFT, kinetic propagator or 4 pi / |G|^2 (with
-//                   1/N^3), inverse z FFT
-//   plane inverse : y then x inverse FFTs of one z-plane; plain store, store plus the induced density
-//                   of the pair's L orbitals (Eq. 11), or the Poisson unpacking with the damped
-//                   time-integral accumulation of Eq. (13)
+// The split-operator step (Eq. 10) takes two sweeps over the orbitals: the kinetic propagator is
+// the product of three one-dimensional operators (one per axis), so
+//   plane kinetic : one z-plane per block (2N threads): fused pre-operation (potential phase), the
+//                   x and then the y operator (forward FFT, exp(-i dt k^2 / 2) / N, inverse FFT)
+//   z kinetic     : 16 columns per warp: the z operator, and for the pair batch the induced density
+//                   of the pair's L orbitals (Eq. 11)
+// The Poisson solves (4 pi / |G|^2 does not factor over the axes) keep the 3D round trip:
+//   plane forward : pre-operation (packing), x FFTs in the padded tile, y FFTs stored to global
+//   z columns     : forward z FFT, 4 pi / |G|^2 with 1/N^3, inverse z FFT
+//   plane inverse : y then x inverse FFTs, then the unpacking with the damped time-integral
+//                   accumulation of Eq. (13) and E - 1 of the next step
 // Blocks are ordered plane-major (plane outer, item inner), so the tables read beside the orbitals
 // (eta0 of each stochastic orbital, the potential phases, E - 1 of each pair) are the same z-slice
 // for consecutive blocks and stay in L2 even when the whole table set does not fit there.
@@ -91,67 +95,40 @@ template <int N, int SIGN> __device__ __forceinline__ void fft2_dif(float2 (&v)[
 }
 
 // the padded plane tile; the density pass adds the pair's density accumulator (N^2 floats)
-// 8-byte asynchronous global -> shared copy (cached in L1 only on the way, i.e. not at all reused)
-__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 template <int N> constexpr size_t split_smem() { return (size_t)N * (N + 1) * sizeof(float2); }
 template <int N> constexpr size_t split_density_smem() { return split_smem<N>() + (size_t)N * N * sizeof(float); }
 
 // ------------------------------------------------------------------------------------------
-// plane forward pass: block = (plane z, item), 2N threads
-
+// The pre-operation of a forward plane pass into the padded tile. Thread t of the 2N covers the
+// points t + k 2N (k < N / 2) of the plane, i.e. row t / N + 2k, column t % N.
 template <int N, bool PAIR>
-__global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<float> g, XfwdArgs<float> a, int n_items) {
+__device__ __forceinline__ void preop_plane(const GView<float> &g, const XfwdArgs<float> &a, long long item,
+                                            long long off, float2 *S) {
   using C = float2;
-  constexpr int LD = N + 1, NN = N * N, NT = 2 * N, H = N / 2, Q = H / 2, KP = NN / NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *S = reinterpret_cast<C *>(smem_raw);
-  const int z = (int)(blockIdx.x / (unsigned)n_items);
-  const long long item = (long long)blockIdx.x - (long long)z * n_items;
-  const long long off = (long long)z * NN;
+  constexpr int LD = N + 1, NT = 2 * N, KP = N / 2, UB = 8;
   const PreopItem<float> it = preop_item<float>(g, a, item);
-  constexpr int UB = 8;
+  const int y0 = threadIdx.x / N;
+  C *srow = S + y0 * LD + (threadIdx.x - y0 * N);
   if constexpr (PAIR) {
-    // the plane of d (the stream from HBM) goes into the tile by asynchronous copies, all at once;
-    // the tables beside it (eta0, the potential phase, E - 1) are the same z-slice for consecutive
-    // blocks and come from L2 in batches while the copies land
-    const C *dp = it.in + off, *ap = it.a + off, *pp = it.pv + off;
-    const C *ep = it.em1 ? it.em1 + off : nullptr;
-#pragma unroll 8
-    for (int k = 0; k < KP; ++k) {
-      const int l = threadIdx.x + k * NT;
-      const int y = l / N, x = l - y * N;
-      cp_async8(S + y * LD + x, dp + l);
-    }
-    cp_async_commit();
-    constexpr int UBP = 16;
+    const C *dp = it.in + off + threadIdx.x, *ap = it.a + off + threadIdx.x, *pp = it.pv + off + threadIdx.x;
+    const C *ep = it.em1 ? it.em1 + off + threadIdx.x : nullptr;
 #pragma unroll 1
-    for (int k0 = 0; k0 < KP; k0 += UBP) {
-      C av[UBP], pv[UBP], ev[UBP];
+    for (int k0 = 0; k0 < KP; k0 += UB) {
+      C dv[UB], av[UB], pv[UB], ev[UB];
 #pragma unroll
-      for (int k = 0; k < UBP; ++k) {
+      for (int k = 0; k < UB; ++k) {
         if (k0 + k < KP) {
-          const int l = threadIdx.x + (k0 + k) * NT;
+          const int l = (k0 + k) * NT;
+          dv[k] = dp[l];
           av[k] = ap[l];
           pv[k] = pp[l];
           ev[k] = ep ? ep[l] : C{0.f, 0.f};
         }
       }
-      if (k0 == 0) cp_async_wait_all();  // this thread's copies (it reads only those back)
 #pragma unroll
-      for (int k = 0; k < UBP; ++k) {
-        if (k0 + k < KP) {
-          const int l = threadIdx.x + (k0 + k) * NT;
-          const int y = l / N, x = l - y * N;
-          C *sp = S + y * LD + x;
-          *sp = pair_phase<float>(pv[k], ev[k], av[k], renorm_value<float>(*sp, av[k], it.cm1));
-        }
-      }
+      for (int k = 0; k < UB; ++k)
+        if (k0 + k < KP)
+          srow[2 * (k0 + k) * LD] = pair_phase<float>(pv[k], ev[k], av[k], renorm_value<float>(dv[k], av[k], it.cm1));
     }
   } else {
     auto run = [&](auto f) {
@@ -162,13 +139,8 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<flo
         for (int k = 0; k < UB; ++k)
           if (k0 + k < KP) v[k] = f(off + threadIdx.x + (k0 + k) * NT);
 #pragma unroll
-        for (int k = 0; k < UB; ++k) {
-          if (k0 + k < KP) {
-            const int l = threadIdx.x + (k0 + k) * NT;
-            const int y = l / N, x = l - y * N;
-            S[y * LD + x] = v[k];
-          }
-        }
+        for (int k = 0; k < UB; ++k)
+          if (k0 + k < KP) srow[2 * (k0 + k) * LD] = v[k];
       }
     };
     if (it.mode == XF_PHASE_A) {
@@ -187,6 +159,27 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<flo
       run([&](long long i) { return preop_at<float>(g, it, i); });
     }
   }
+}
+
+// the per-axis kinetic factor exp(-i k_m^2 dt / 2) / N of frequency index m
+__device__ __forceinline__ float2 kin_axis(const GView<float> &g, int m, float inv_n) {
+  return cscale(g.kin[m], inv_n);
+}
+
+// ------------------------------------------------------------------------------------------
+// plane forward pass of the three-pass round trip (Poisson packing of densities and pair
+// products): block = (plane z, item), 2N threads; x FFTs in the tile, y FFTs stored to global
+
+template <int N>
+__global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<float> g, XfwdArgs<float> a, int n_items) {
+  using C = float2;
+  constexpr int LD = N + 1, NN = N * N, H = N / 2, Q = H / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  const int z = (int)(blockIdx.x / (unsigned)n_items);
+  const long long item = (long long)blockIdx.x - (long long)z * n_items;
+  const long long off = (long long)z * NN;
+  preop_plane<N, false>(g, a, item, off, S);
   __syncthreads();
   const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
   {  // x transforms, pencil p = row p of the tile, in place
@@ -215,6 +208,121 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<flo
       out[(s * Q + j) * N] = v[j];
       out[(H + s * Q + j) * N] = v[Q + j];
     }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// First sweep of the two-sweep split-operator step. The kinetic propagator of Eq. (10) is
+// exp(-i dt |G|^2 / 2) = prod_axes exp(-i dt k_a^2 / 2), so in real space it is the product of three
+// one-dimensional operators F_a^-1 K_a F_a, one per axis, which commute. This pass applies the
+// potential phase (the pre-operation) and the x and y operators to one z-plane held in shared
+// memory (forward FFT, K_a / N, inverse FFT along each axis); the second sweep applies the z
+// operator. One HBM round trip per sweep: two per step instead of the three of a 3D FFT round trip.
+
+template <int N, bool PAIR>
+__global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_kin2(GView<float> g, XfwdArgs<float> a, int n_items) {
+  using C = float2;
+  constexpr int LD = N + 1, NN = N * N, H = N / 2, Q = H / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  const int z = (int)(blockIdx.x / (unsigned)n_items);
+  const long long item = (long long)blockIdx.x - (long long)z * n_items;
+  const long long off = (long long)z * NN;
+  preop_plane<N, PAIR>(g, a, item, off, S);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
+  const float inv_n = 1.f / (float)N;
+  {  // x operator on row p, in place
+    C v[H];
+    C *row = S + p * LD;
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = row[2 * m + s];
+    fft2_dit<N, -1>(v, s);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      v[j] = cmul(v[j], kin_axis(g, s * Q + j, inv_n));
+      v[Q + j] = cmul(v[Q + j], kin_axis(g, H + s * Q + j, inv_n));
+    }
+    fft2_dif<N, +1>(v, s);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < H; ++m) row[2 * m + s] = v[m];
+  }
+  __syncthreads();
+  {  // y operator on column p, stored to global
+    C v[H];
+    const C *col = S + p;
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = col[(2 * m + s) * LD];
+    fft2_dit<N, -1>(v, s);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      v[j] = cmul(v[j], kin_axis(g, s * Q + j, inv_n));
+      v[Q + j] = cmul(v[Q + j], kin_axis(g, H + s * Q + j, inv_n));
+    }
+    fft2_dif<N, +1>(v, s);
+    C *out = a.out + item * g.ng + off + p;
+#pragma unroll
+    for (int m = 0; m < H; ++m) out[(2 * m + s) * N] = v[m];
+  }
+}
+
+// Second sweep: the z operator on 64 columns of one item (PLAIN) or of each of the L orbitals of a
+// pair (DENS), which also sums the pair's induced density 2 sum_l (2 Re(conj(eta0_l) d_l) +
+// |d_l|^2) (Eq. 11) in shared memory and writes it.
+constexpr int kZDPitch = 80;  // density rows of 64 columns padded so the two half-warps miss each other's banks
+
+template <int N, bool DENS>
+__global__ void __launch_bounds__(128, 3) k_zkin2(GView<float> g, float2 *data, const float2 *a_next, float *dens,
+                                                  int n_units, int L) {
+  using C = float2;
+  constexpr int NN = N * N, H = N / 2, Q = H / 2, UB = 16;
+  __shared__ float D[DENS ? N * kZDPitch : 1];
+  const int cs = (int)(blockIdx.x / (unsigned)n_units);
+  const int unit = (int)blockIdx.x - cs * n_units;
+  const int lane = threadIdx.x & 31, s = lane >> 4, cw = (threadIdx.x >> 5) * 16 + (lane & 15);
+  const int rem = cs * 64 + cw;
+  const float inv_n = 1.f / (float)N;
+  const int n_orb = DENS ? L : 1;
+  for (int ell = 0; ell < n_orb; ++ell) {
+    const long long item = DENS ? (long long)unit * L + ell : unit;
+    C *base = data + item * g.ng + rem;
+    C v[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = base[(long long)(2 * m + s) * NN];
+    fft2_dit<N, -1>(v, s);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      v[j] = cmul(v[j], kin_axis(g, s * Q + j, inv_n));
+      v[Q + j] = cmul(v[Q + j], kin_axis(g, H + s * Q + j, inv_n));
+    }
+    fft2_dif<N, +1>(v, s);
+#pragma unroll
+    for (int m = 0; m < H; ++m) base[(long long)(2 * m + s) * NN] = v[m];
+    if constexpr (DENS) {
+      const C *ab = a_next + (long long)ell * g.ng + rem;
+#pragma unroll
+      for (int m0 = 0; m0 < H; m0 += UB) {
+        C a0[UB];
+#pragma unroll
+        for (int k = 0; k < UB; ++k)
+          if (m0 + k < H) a0[k] = ab[(long long)(2 * (m0 + k) + s) * NN];
+#pragma unroll
+        for (int k = 0; k < UB; ++k) {
+          if (m0 + k < H) {
+            const C dv = v[m0 + k];
+            const float t = 2.f * (2.f * (a0[k].x * dv.x + a0[k].y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+            float &acc = D[(2 * (m0 + k) + s) * kZDPitch + cw];
+            acc = ell ? acc + t : t;
+          }
+        }
+      }
+    }
+  }
+  if constexpr (DENS) {
+    float *db = dens + (long long)unit * g.ng + rem;
+#pragma unroll 8
+    for (int m = 0; m < H; ++m) db[(long long)(2 * m + s) * NN] = D[(2 * m + s) * kZDPitch + cw];
   }
 }
 
@@ -259,33 +367,36 @@ __global__ void __launch_bounds__(128, 4) k_zcol2(GView<float> g, float2 *data, 
 }
 
 // ------------------------------------------------------------------------------------------
-// plane inverse pass: block = (plane z, unit), unit = pair (DENSITY) or item (PLAIN, POISSON)
+// plane inverse pass of the Poisson round trip: block = (plane z, packed slot). y then x inverse
+// FFTs of the plane, then the epilogue: the two real potentials of the slot, u, the damped time
+// integral of Eq. (13) and E - 1 for the next step.
 
-enum { SP_PLAIN = 0, SP_DENSITY = 1, SP_POISSON = 2 };
-
-// y inverse FFTs of plane z of `src` (global, frequency blocks) into the tile (interleaved rows),
-// then x inverse FFTs in the tile; ends with the tile complete
-// (the block barrier before the tile is written lets the column loads and y FFTs of this plane
-// overlap the previous use of the tile by other warps)
 template <int N>
-__device__ __forceinline__ void inverse_plane2(float2 *S, const float2 *src, int s, int p) {
+__global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_inv2(GView<float> g, float2 *data, float *u_out,
+                                                                       float *acc, float2 *em1_out, int n_units,
+                                                                       PoissonOut po) {
   using C = float2;
-  constexpr int LD = N + 1, H = N / 2, Q = H / 2;
-  {
+  constexpr int LD = N + 1, NN = N * N, NT = 2 * N, H = N / 2, Q = H / 2, KP = NN / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *S = reinterpret_cast<C *>(smem_raw);
+  const int z = (int)(blockIdx.x / (unsigned)n_units);
+  const long long item = (long long)blockIdx.x - (long long)z * n_units;
+  const long long off = (long long)z * NN;
+  const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
+  {  // y inverse FFTs from global (frequency blocks) into the tile (interleaved rows)
     C v[H];
-    const C *col = src + p;
+    const C *col = data + item * g.ng + off + p;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
       v[j] = col[(s * Q + j) * N];
       v[Q + j] = col[(H + s * Q + j) * N];
     }
     fft2_dif<N, +1>(v, s);
-    __syncthreads();
 #pragma unroll
     for (int m = 0; m < H; ++m) S[(2 * m + s) * LD + p] = v[m];
   }
   __syncthreads();
-  {
+  {  // x inverse FFTs in the tile
     C v[H];
     C *row = S + p * LD;
 #pragma unroll
@@ -299,91 +410,37 @@ __device__ __forceinline__ void inverse_plane2(float2 *S, const float2 *src, int
     for (int m = 0; m < H; ++m) row[2 * m + s] = v[m];
   }
   __syncthreads();
-}
-
-template <int N, int MODE>
-__global__ void __launch_bounds__(2 * N, (MODE == SP_DENSITY || N == 96) ? 2 : 3) k_plane_inv2(GView<float> g, float2 *data, const float2 *a_next,
-                                                      float *dens, float *u_out, float *acc, float2 *em1_out,
-                                                      int n_units, int L, PoissonOut po) {
-  using C = float2;
-  constexpr int LD = N + 1, NN = N * N, NT = 2 * N, KP = NN / NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *S = reinterpret_cast<C *>(smem_raw);
-  const int z = (int)(blockIdx.x / (unsigned)n_units);
-  const int unit = (int)blockIdx.x - z * n_units;
-  const long long off = (long long)z * NN;
-  const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
-  if constexpr (MODE == SP_DENSITY) {
-    // induced density 2 sum_l (2 Re(conj(eta0_l) d_l) + |d_l|^2) of the pair (Eq. 11), summed in
-    // shared memory behind the tile (registers hold the pencils)
-    float *D = reinterpret_cast<float *>(S + N * LD);
-    for (int ell = 0; ell < L; ++ell) {
-      const long long item = (long long)unit * L + ell;
-      C *base = data + item * g.ng + off;
-      inverse_plane2<N>(S, base, s, p);
-      const C *ab = a_next + (long long)ell * g.ng + off;
-      // every eta0 load of the epilogue in flight at once (the pencil registers are free here)
-      C a0[KP];
-#pragma unroll
-      for (int k = 0; k < KP; ++k) a0[k] = ab[threadIdx.x + k * NT];
-#pragma unroll
-      for (int k = 0; k < KP; ++k) {
-        const int l = threadIdx.x + k * NT;
-        const int y = l / N, x = l - y * N;
-        const C dv = S[y * LD + x];
-        base[l] = dv;
-        const float t = 2.f * (2.f * (a0[k].x * dv.x + a0[k].y * dv.y) + dv.x * dv.x + dv.y * dv.y);
-        D[l] = ell ? D[l] + t : t;
-      }
-    }
-    __syncthreads();
-    float *db = dens + (long long)unit * g.ng + off;
-#pragma unroll 4
-    for (int k = 0; k < KP; ++k) db[threadIdx.x + k * NT] = D[threadIdx.x + k * NT];
-  } else if constexpr (MODE == SP_PLAIN) {
-    C *base = data + (long long)unit * g.ng + off;
-    inverse_plane2<N>(S, base, s, p);
-#pragma unroll 4
-    for (int k = 0; k < KP; ++k) {
-      const int l = threadIdx.x + k * NT;
-      const int y = l / N, x = l - y * N;
-      base[l] = S[y * LD + x];
-    }
-  } else {
-    // Poisson epilogue: the two real potentials of the slot; u, the damped time integral, E - 1
-    const long long item = unit;
-    inverse_plane2<N>(S, data + item * g.ng + off, s, p);
-    const float coef = (float)po.coef, tau = (float)po.tau_next;
-    const bool keep = po.keep != 0.0;
-    const int n_h = (2 * item + 1 < po.n_out) ? 2 : 1;
-    constexpr int UB = 8;
+  const float coef = (float)po.coef, tau = (float)po.tau_next;
+  const bool keep = po.keep != 0.0;
+  const int n_h = (2 * item + 1 < po.n_out) ? 2 : 1;
+  const int y0 = threadIdx.x / N;
+  const C *srow = S + y0 * LD + (threadIdx.x - y0 * N);
+  constexpr int UB = 8;
 #pragma unroll 1
-    for (int k0 = 0; k0 < KP; k0 += UB) {
-      C v[UB];
-      float old[UB][2];
+  for (int k0 = 0; k0 < KP; k0 += UB) {
+    C v[UB];
+    float old[UB][2];
 #pragma unroll
-      for (int k = 0; k < UB; ++k) {
-        if (k0 + k >= KP) break;
-        const int l = threadIdx.x + (k0 + k) * NT;
-        const int y = l / N, x = l - y * N;
-        v[k] = S[y * LD + x];
+    for (int k = 0; k < UB; ++k) {
+      if (k0 + k >= KP) break;
+      const int l = threadIdx.x + (k0 + k) * NT;
+      v[k] = srow[2 * (k0 + k) * LD];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          old[k][h] = (acc && keep && h < n_h) ? acc[(2 * item + h) * g.ng + off + l] : 0.f;
-      }
+      for (int h = 0; h < 2; ++h)
+        old[k][h] = (acc && keep && h < n_h) ? acc[(2 * item + h) * g.ng + off + l] : 0.f;
+    }
 #pragma unroll
-      for (int k = 0; k < UB; ++k) {
-        if (k0 + k >= KP) break;
-        const int l = threadIdx.x + (k0 + k) * NT;
+    for (int k = 0; k < UB; ++k) {
+      if (k0 + k >= KP) break;
+      const int l = threadIdx.x + (k0 + k) * NT;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h >= n_h) break;
-          const float val = h ? v[k].y : v[k].x;
-          const long long o = (2 * item + h) * g.ng + off + l;
-          if (u_out) u_out[o] = val;
-          if (acc) acc[o] = old[k][h] + coef * val;
-          if (em1_out) em1_out[o] = phase_em1<float>(val, tau);
-        }
+      for (int h = 0; h < 2; ++h) {
+        if (h >= n_h) break;
+        const float val = h ? v[k].y : v[k].x;
+        const long long o = (2 * item + h) * g.ng + off + l;
+        if (u_out) u_out[o] = val;
+        if (acc) acc[o] = old[k][h] + coef * val;
+        if (em1_out) em1_out[o] = phase_em1<float>(val, tau);
       }
     }
   }
@@ -391,20 +448,22 @@ __global__ void __launch_bounds__(2 * N, (MODE == SP_DENSITY || N == 96) ? 2 : 3
 
 template <int N> void set_split_attrs() {
   const int sm = (int)split_smem<N>();
-  cudaFuncSetAttribute(k_plane_fwd2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_plane_fwd2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_plane_inv2<N, SP_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_plane_inv2<N, SP_DENSITY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)split_density_smem<N>());
-  cudaFuncSetAttribute(k_plane_inv2<N, SP_POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_fwd2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_kin2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_kin2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_plane_inv2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 template <int N> void fwd2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s) {
+  k_plane_fwd2<N><<<(unsigned)a.n_items * N, 2 * N, split_smem<N>(), s>>>(view(g), a, a.n_items);
+}
+
+template <int N> void kin2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s) {
   const unsigned blocks = (unsigned)a.n_items * N;
   if (a.mode == XF_PHASE_PAIR)
-    k_plane_fwd2<N, true><<<blocks, 2 * N, split_smem<N>(), s>>>(view(g), a, a.n_items);
+    k_plane_kin2<N, true><<<blocks, 2 * N, split_smem<N>(), s>>>(view(g), a, a.n_items);
   else
-    k_plane_fwd2<N, false><<<blocks, 2 * N, split_smem<N>(), s>>>(view(g), a, a.n_items);
+    k_plane_kin2<N, false><<<blocks, 2 * N, split_smem<N>(), s>>>(view(g), a, a.n_items);
 }
 
 template <int N> void zcol2(const GridTables<float> &g, float2 *d, int n_items, int mult, cudaStream_t s) {
@@ -414,19 +473,21 @@ template <int N> void zcol2(const GridTables<float> &g, float2 *d, int n_items, 
 }
 
 template <int N>
-void inv2(const GridTables<float> &g, float2 *d, int n_units, const float2 *a_next, int L, float *dens,
-          float *u_out, float *acc, float2 *em1_out, const PoissonOut &po, int mode, cudaStream_t s) {
-  const unsigned blocks = (unsigned)n_units * N;
-  const size_t sm = split_smem<N>();
-  if (mode == SP_DENSITY)
-    k_plane_inv2<N, SP_DENSITY><<<blocks, 2 * N, split_density_smem<N>(), s>>>(view(g), d, a_next, dens, nullptr, nullptr, nullptr,
-                                                         n_units, L, po);
-  else if (mode == SP_PLAIN)
-    k_plane_inv2<N, SP_PLAIN><<<blocks, 2 * N, sm, s>>>(view(g), d, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                       n_units, 1, po);
+void zkin2(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L, float *dens,
+           cudaStream_t s) {
+  const int units = dens ? n_items / L : n_items;
+  const unsigned blocks = (unsigned)units * (N * N / 64);
+  if (dens)
+    k_zkin2<N, true><<<blocks, 128, 0, s>>>(view(g), d, a_next, dens, units, L);
   else
-    k_plane_inv2<N, SP_POISSON><<<blocks, 2 * N, sm, s>>>(view(g), d, nullptr, nullptr, u_out, acc, em1_out,
-                                                         n_units, 1, po);
+    k_zkin2<N, false><<<blocks, 128, 0, s>>>(view(g), d, nullptr, nullptr, units, 1);
+}
+
+template <int N>
+void inv2(const GridTables<float> &g, float2 *d, int n_units, float *u_out, float *acc, float2 *em1_out,
+          const PoissonOut &po, cudaStream_t s) {
+  k_plane_inv2<N><<<(unsigned)n_units * N, 2 * N, split_smem<N>(), s>>>(view(g), d, u_out, acc, em1_out, n_units,
+                                                                      po);
 }
 
 }  // namespace
@@ -460,19 +521,21 @@ void launch_zcol2(const GridTables<float> &g, float2 *d, int n_items, int mult, 
   else if (g.N == 96) zcol2<96>(g, d, n_items, mult, s);
 }
 
-void launch_plane_inv2_orb(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L,
-                           float *dens, cudaStream_t s) {
-  const PoissonOut po{0, 0.0, 0.0, 0.0};
-  const int mode = dens ? SP_DENSITY : SP_PLAIN;
-  const int units = dens ? n_items / L : n_items;
-  if (g.N == 80) inv2<80>(g, d, units, a_next, L, dens, nullptr, nullptr, nullptr, po, mode, s);
-  else if (g.N == 96) inv2<96>(g, d, units, a_next, L, dens, nullptr, nullptr, nullptr, po, mode, s);
-}
-
 void launch_plane_inv2_poisson(const GridTables<float> &g, float2 *d, int n_slots, const PoissonOut &po,
                                float *u_out, float *acc, float2 *em1_out, cudaStream_t s) {
-  if (g.N == 80) inv2<80>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, em1_out, po, SP_POISSON, s);
-  else if (g.N == 96) inv2<96>(g, d, n_slots, nullptr, 1, nullptr, u_out, acc, em1_out, po, SP_POISSON, s);
+  if (g.N == 80) inv2<80>(g, d, n_slots, u_out, acc, em1_out, po, s);
+  else if (g.N == 96) inv2<96>(g, d, n_slots, u_out, acc, em1_out, po, s);
+}
+
+void launch_plane_kin2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s) {
+  if (g.N == 80) kin2<80>(g, a, s);
+  else if (g.N == 96) kin2<96>(g, a, s);
+}
+
+void launch_zkin2(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L, float *dens,
+                  cudaStream_t s) {
+  if (g.N == 80) zkin2<80>(g, d, n_items, a_next, L, dens, s);
+  else if (g.N == 96) zkin2<96>(g, d, n_items, a_next, L, dens, s);
 }
 
 }  // namespace sbse

@@ -77,12 +77,17 @@ struct PoissonOut {
 template <typename T> void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots,
                                                     const PoissonOut &po, T *u_out, T *acc,
                                                     C2<T> *em1_out, cudaStream_t s);
+// split sizes (fft_split.cu): the Poisson round trip (packing modes of XfwdArgs, Z_POISSON)
 void launch_plane_fwd2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s);
 void launch_zcol2(const GridTables<float> &g, float2 *d, int n_items, int mult, cudaStream_t s);
-void launch_plane_inv2_orb(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L,
-                           float *dens, cudaStream_t s);
 void launch_plane_inv2_poisson(const GridTables<float> &g, float2 *d, int n_slots, const PoissonOut &po,
                                float *u_out, float *acc, float2 *em1_out, cudaStream_t s);
+// split sizes: the two sweeps of a split-operator step of the orbitals (XF_PHASE_A / XF_PHASE_PAIR
+// pre-operation + x and y kinetic operators; z kinetic operator + the pairs' induced density when
+// dens != null, L orbitals per pair)
+void launch_plane_kin2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s);
+void launch_zkin2(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L, float *dens,
+                  cudaStream_t s);
 // out = exp(-i V_loc tau), computed in FP64 from the FP64 potential v64
 template <typename T> void launch_phase_table(const double *v64, long long ng, double tau, C2<T> *out,
                                               cudaStream_t s);

@@ -315,6 +315,24 @@ void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T
   // the pair batch (dens != null) times each pass separately when profiling (phases 5, 6, 7)
   const bool sub = dens != nullptr && st == ctx->stream;
   size_t ck = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (split_size(g.N)) {
+      // two sweeps: potential phase + x, y kinetic operators; z kinetic operator (+ density)
+      if (parts & RT_FWD_Z) {
+        if (sub) clk_begin(ctx, 5, &ck);
+        launch_plane_kin2(g, fa, st);
+        count_launch(1);
+        if (sub) clk_end(ctx, ck);
+      }
+      if (parts & RT_INV) {
+        if (sub) clk_begin(ctx, 7, &ck);
+        launch_zkin2(g, data, n_items, a_next, L, dens, st);
+        count_launch(1);
+        if (sub) clk_end(ctx, ck);
+      }
+      return;
+    }
+  }
   if (fast_supported<T>(g.N)) {
     if (parts & RT_FWD_Z) {
       if (sub) clk_begin(ctx, 5, &ck);
