@@ -95,6 +95,25 @@ template <int N, int SIGN> __device__ __forceinline__ void fft2_dif(float2 (&v)[
 }
 
 // the padded plane tile; the density pass adds the pair's density accumulator (N^2 floats)
+// One-dimensional kinetic operator F^-1 diag(K / N) F on the pencil held by a lane pair, without
+// leaving registers: on entry lane s holds x[2m + s], on return y[2m + s] (y = F^-1 K F x / N). Each
+// lane takes the half-length transform of its samples (E for the even ones, O for the odd ones),
+// receives the other lane's, forms E Kp + O M1 (lane 0: even outputs) or O Kp + E M2 (lane 1: odd
+// outputs), and transforms back. tab = [Kp | M1 | M2], N/2 entries each (see set_kinetic).
+template <int N>
+__device__ __forceinline__ void kin_roundtrip(float2 (&v)[N / 2], int s, const float2 *tab) {
+  constexpr int H = N / 2;
+  fft_reg<float, H, -1, TwS>(v);
+  const float2 *mt = tab + (s ? 2 * H : H);
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float2 o = shfl_pair(v[k]);
+    const float2 kp = tab[k], mk = mt[k];
+    v[k] = cadd(cmul(v[k], kp), cmul(o, mk));
+  }
+  fft_reg<float, H, +1, TwS>(v);
+}
+
 template <int N> constexpr size_t split_smem() { return (size_t)N * (N + 1) * sizeof(float2); }
 template <int N> constexpr size_t split_density_smem() { return split_smem<N>() + (size_t)N * N * sizeof(float); }
 
@@ -161,11 +180,6 @@ __device__ __forceinline__ void preop_plane(const GView<float> &g, const XfwdArg
   }
 }
 
-// the per-axis kinetic factor exp(-i k_m^2 dt / 2) / N of frequency index m
-__device__ __forceinline__ float2 kin_axis(const GView<float> &g, int m, float inv_n) {
-  return cscale(g.kin[m], inv_n);
-}
-
 // ------------------------------------------------------------------------------------------
 // plane forward pass of the three-pass round trip (Poisson packing of densities and pair
 // products): block = (plane z, item), 2N threads; x FFTs in the tile, y FFTs stored to global
@@ -216,8 +230,7 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<flo
 // exp(-i dt |G|^2 / 2) = prod_axes exp(-i dt k_a^2 / 2), so in real space it is the product of three
 // one-dimensional operators F_a^-1 K_a F_a, one per axis, which commute. This pass applies the
 // potential phase (the pre-operation) and the x and y operators to one z-plane held in shared
-// memory (forward FFT, K_a / N, inverse FFT along each axis); the second sweep applies the z
-// operator. One HBM round trip per sweep: two per step instead of the three of a 3D FFT round trip.
+// memory (kin_roundtrip along each axis); the second sweep applies the z operator. One HBM round trip per sweep: two per step instead of the three of a 3D FFT round trip.
 
 template <int N, bool PAIR>
 __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_kin2(GView<float> g, XfwdArgs<float> a, int n_items) {
@@ -228,22 +241,17 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_kin2(GView<flo
   const int z = (int)(blockIdx.x / (unsigned)n_items);
   const long long item = (long long)blockIdx.x - (long long)z * n_items;
   const long long off = (long long)z * NN;
+  __shared__ C tab[3 * H];
+  for (int i = threadIdx.x; i < 3 * H; i += blockDim.x) tab[i] = g.kin[N + i];
   preop_plane<N, PAIR>(g, a, item, off, S);
   __syncthreads();
   const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
-  const float inv_n = 1.f / (float)N;
   {  // x operator on row p, in place
     C v[H];
     C *row = S + p * LD;
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = row[2 * m + s];
-    fft2_dit<N, -1>(v, s);
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      v[j] = cmul(v[j], kin_axis(g, s * Q + j, inv_n));
-      v[Q + j] = cmul(v[Q + j], kin_axis(g, H + s * Q + j, inv_n));
-    }
-    fft2_dif<N, +1>(v, s);
+    kin_roundtrip<N>(v, s, tab);
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < H; ++m) row[2 * m + s] = v[m];
@@ -254,13 +262,7 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_kin2(GView<flo
     const C *col = S + p;
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = col[(2 * m + s) * LD];
-    fft2_dit<N, -1>(v, s);
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      v[j] = cmul(v[j], kin_axis(g, s * Q + j, inv_n));
-      v[Q + j] = cmul(v[Q + j], kin_axis(g, H + s * Q + j, inv_n));
-    }
-    fft2_dif<N, +1>(v, s);
+    kin_roundtrip<N>(v, s, tab);
     C *out = a.out + item * g.ng + off + p;
 #pragma unroll
     for (int m = 0; m < H; ++m) out[(2 * m + s) * N] = v[m];
@@ -276,13 +278,15 @@ template <int N, bool DENS>
 __global__ void __launch_bounds__(128, 3) k_zkin2(GView<float> g, float2 *data, const float2 *a_next, float *dens,
                                                   int n_units, int L) {
   using C = float2;
-  constexpr int NN = N * N, H = N / 2, Q = H / 2, UB = 16;
+  constexpr int NN = N * N, H = N / 2, UB = 16;
   __shared__ float D[DENS ? N * kZDPitch : 1];
+  __shared__ C tab[3 * H];
+  for (int i = threadIdx.x; i < 3 * H; i += blockDim.x) tab[i] = g.kin[N + i];
+  __syncthreads();
   const int cs = (int)(blockIdx.x / (unsigned)n_units);
   const int unit = (int)blockIdx.x - cs * n_units;
   const int lane = threadIdx.x & 31, s = lane >> 4, cw = (threadIdx.x >> 5) * 16 + (lane & 15);
   const int rem = cs * 64 + cw;
-  const float inv_n = 1.f / (float)N;
   const int n_orb = DENS ? L : 1;
   for (int ell = 0; ell < n_orb; ++ell) {
     const long long item = DENS ? (long long)unit * L + ell : unit;
@@ -290,13 +294,7 @@ __global__ void __launch_bounds__(128, 3) k_zkin2(GView<float> g, float2 *data, 
     C v[H];
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = base[(long long)(2 * m + s) * NN];
-    fft2_dit<N, -1>(v, s);
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      v[j] = cmul(v[j], kin_axis(g, s * Q + j, inv_n));
-      v[Q + j] = cmul(v[Q + j], kin_axis(g, H + s * Q + j, inv_n));
-    }
-    fft2_dif<N, +1>(v, s);
+    kin_roundtrip<N>(v, s, tab);
 #pragma unroll
     for (int m = 0; m < H; ++m) base[(long long)(2 * m + s) * NN] = v[m];
     if constexpr (DENS) {
@@ -316,6 +314,8 @@ __global__ void __launch_bounds__(128, 3) k_zkin2(GView<float> g, float2 *data, 
             acc = ell ? acc + t : t;
           }
         }
+        // keep the loads of the next batch below this one (hoisting them all costs registers)
+        asm volatile("" ::: "memory");
       }
     }
   }

@@ -14,7 +14,8 @@ template <typename T> struct GridTables {
   long long ng = 0;
   FftPlan plan{};
   C2<T> *tw = nullptr;      // exp(-2 pi i k / N), k < N
-  C2<T> *kin = nullptr;     // exp(-i k_m^2 dt / 2) per axis index m (rebuilt per dt)
+  C2<T> *kin = nullptr;     // exp(-i k_m^2 dt / 2) per axis index m (rebuilt per dt); for even N
+                            // followed by the lane-pair round-trip multipliers Kp, M1, M2 (N/2 each)
   T *k2 = nullptr;          // k_m^2 per axis index m
   T *v_loc = nullptr;       // V_loc(r), ng
   C2<T> *pv_dt = nullptr;   // exp(-i V_loc dt), ng (rebuilt per dt)

@@ -226,7 +226,8 @@ template <typename T> int build_tables(sbse_ctx *ctx, GridTables<T> &g, const do
   }
   int rc;
   if ((rc = dalloc(ctx, &g.tw, N * sizeof(C2<T>)))) return rc;
-  if ((rc = dalloc(ctx, &g.kin, N * sizeof(C2<T>)))) return rc;
+  // per-axis kinetic factors (N), then for even N the lane-pair round-trip multipliers (3 N / 2)
+  if ((rc = dalloc(ctx, &g.kin, (N + 3 * (N / 2)) * sizeof(C2<T>)))) return rc;
   if ((rc = dalloc(ctx, &g.k2, N * sizeof(T)))) return rc;
   if ((rc = dalloc(ctx, &g.v_loc, ctx->ng * sizeof(T)))) return rc;
   if ((rc = dalloc(ctx, &g.pv_dt, ctx->ng * sizeof(C2<T>)))) return rc;
@@ -242,13 +243,31 @@ template <typename T> int build_tables(sbse_ctx *ctx, GridTables<T> &g, const do
 
 // kinetic propagator per axis: exp(-i k_m^2 dt / 2); the 3D factor is the product over axes
 template <typename T> int set_kinetic(sbse_ctx *ctx, GridTables<T> &g, double dt) {
-  std::vector<C2<T>> kin(ctx->N);
-  for (int m = 0; m < ctx->N; ++m) {
-    const double kk = kval(m, ctx->N, ctx->box);
+  const int N = ctx->N, H = N / 2;
+  std::vector<C2<T>> kin(N + 3 * H);
+  std::vector<double> kr(N), ki(N);
+  for (int m = 0; m < N; ++m) {
+    const double kk = kval(m, N, ctx->box);
     const double ph = -0.5 * dt * kk * kk;
-    kin[m] = C2<T>{(T)cos(ph), (T)sin(ph)};
+    kr[m] = cos(ph);
+    ki[m] = sin(ph);
+    kin[m] = C2<T>{(T)kr[m], (T)ki[m]};
   }
-  CK(cudaMemcpyAsync(g.kin, kin.data(), ctx->N * sizeof(C2<T>), cudaMemcpyHostToDevice, ctx->stream));
+  // The one-dimensional kinetic operator F^-1 diag(K) F on the even and odd samples (one per lane
+  // of a lane pair): with E, O the half-length transforms, the even outputs are the inverse
+  // half-length transform of E Kp + O M1 and the odd ones of O Kp + E M2, where
+  // Kp = (K_k + K_k+H) / N, M1 = W^k (K_k - K_k+H) / N, M2 = W^-k (K_k - K_k+H) / N, W = exp(-2 pi i / N).
+  if (N % 2 == 0) {
+    for (int k = 0; k < H; ++k) {
+      const double pr = (kr[k] + kr[k + H]) / N, pi = (ki[k] + ki[k + H]) / N;
+      const double mr = (kr[k] - kr[k + H]) / N, mi = (ki[k] - ki[k + H]) / N;
+      const double wr = cos(-2.0 * M_PI * k / N), wi = sin(-2.0 * M_PI * k / N);
+      kin[N + k] = C2<T>{(T)pr, (T)pi};
+      kin[N + H + k] = C2<T>{(T)(wr * mr - wi * mi), (T)(wr * mi + wi * mr)};
+      kin[N + 2 * H + k] = C2<T>{(T)(wr * mr + wi * mi), (T)(wr * mi - wi * mr)};
+    }
+  }
+  CK(cudaMemcpyAsync(g.kin, kin.data(), kin.size() * sizeof(C2<T>), cudaMemcpyHostToDevice, ctx->stream));
   // potential factors exp(-i V dt) (two merged half steps) and exp(-i V dt / 2)
   launch_phase_table<T>(ctx->v64, ctx->ng, dt, g.pv_dt, ctx->stream);
   launch_phase_table<T>(ctx->v64, ctx->ng, 0.5 * dt, g.pv_half, ctx->stream);
