@@ -517,20 +517,22 @@ def main():
                      "tdh_ms_per_pair_this_workload": ms_step / blk}
 
     # Roofline. Algorithmic unit: one read and one write of every complex value of the propagated
-    # block (blk L n_g points, 16 B/point in FP32). Each of the three passes of a TDH step (phases
-    # 5, 6, 7, timed by events on the library's stream) is one such sweep; the dominant kernel is
-    # the pass with the largest share. The whole propagation step (phase 0) is reported against the
-    # same per-step figure, so its fraction shows the cost of three sweeps per step.
+    # block (blk L n_g points, 16 B/point in FP32). Each pass of a TDH step (phases 5, 6, 7, timed by
+    # events on the library's stream; two passes on the 80/96 grids, three elsewhere) is one such
+    # sweep; the dominant kernel is the pass with the largest share. The whole propagation step
+    # (phase 0) is reported against the same per-step figure, so its fraction shows the cost of
+    # several sweeps per step.
     peak, src = measured_peaks()
     csize = 8 if prec == B.SBSE_MIXED else 16
     sweep_bytes = blk * pre.n_s * pre.N ** 3 * 2 * csize
     split = pre.N in (80, 96)
-    pass_names = {5: "forward plane pass " + ("k_plane_fwd2" if split else "k_plane_fwd") +
-                     " (potential phase + x, y FFTs)",
-                  6: "z-column pass " + ("k_zcol2" if split else "k_zcol_tma") +
-                     " (z FFT, kinetic phase, inverse z FFT)",
-                  7: "inverse plane pass " + ("k_plane_inv2" if split else "k_plane_inv_density_tma") +
-                     " (y, x inverse FFTs + density)"}
+    if split:  # two sweeps per step: the kinetic propagator as three one-dimensional operators
+        pass_names = {5: "plane kinetic pass k_plane_kin2 (potential phase + x, y kinetic operators)",
+                      7: "z kinetic pass k_zkin2 (z kinetic operator + induced density)"}
+    else:
+        pass_names = {5: "forward plane pass k_plane_fwd (potential phase + x, y FFTs)",
+                      6: "z-column pass k_zcol_tma (z FFT, kinetic phase, inverse z FFT)",
+                      7: "inverse plane pass k_plane_inv_density_tma (y, x inverse FFTs + density)"}
     passes = {}
     for ph, name in pass_names.items():
         t, nl = phase[ph]
