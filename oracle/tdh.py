@@ -207,7 +207,7 @@ def clean(a, d, phi_occ, n0, grid: Grid):
 
 
 def tdh_w_pol(grid: Grid, v_loc, phi_occ, rho, coeff, p: TDHParams, coulomb=coulomb_periodic,
-              record=None):
+              record=None, observe=None):
     """Stochastic-TDH W^pol_ij(r) of Eq. (13) for the source density rho = phi_i phi_j.
 
     Steps (difference form; algebraically the same as propagating eta^alpha and eta^0, Sec. II.B):
@@ -219,7 +219,9 @@ def tdh_w_pol(grid: Grid, v_loc, phi_occ, rho, coeff, p: TDHParams, coulomb=coul
       state (reading: the time at which u enters a step), half potential step with u_{n+1}.
       Finally accumulate u_{N_t}. u subtracts the density of the unperturbed set propagated with
       the same H0 (reading of Eq. 11 for stochastic orbitals, which are not stationary).
-    Returns W^pol (N, N, N). `record`, if a list, receives (n, u_n) for every accumulated sample.
+    Returns W^pol (N, N, N). `record`, if a list, receives (n, u_n) for every accumulated sample;
+    `observe`, if given, is called as observe(n + 1, a, d) with the state after each completed step
+    (read-only views; nothing it returns is used).
     """
     wts = time_weights(p)
     prop = _Propagator(grid, v_loc, p.dt)
@@ -246,6 +248,8 @@ def tdh_w_pol(grid: Grid, v_loc, phi_occ, rho, coeff, p: TDHParams, coulomb=coul
         u = potential(a, d)
         up = u if p.feedback else 0.0 * u
         a, d = prop.half_phase_pair(a, d, up)
+        if observe is not None:
+            observe(n + 1, a, d)
     w += (wts[p.n_steps] / p.alpha) * u
     if record is not None:
         record.append((p.n_steps, u.copy()))

@@ -182,3 +182,72 @@ def test_deterministic_w_pol_is_symmetric_and_screens(tiny8):
                 bare = np.sum(r * tdh.coulomb_periodic(r, g)) * g.dV
                 assert pol < 0.0 and 0.0 < bare + pol < bare
         assert asym[1] < 1e-4 and 3.5 < asym[0] / asym[1] < 4.5
+
+
+def test_tdh_energy_is_conserved_to_second_order_in_dt(tiny8):
+    """Time-dependent Hartree conserves E = 2 sum_s <psi_s|H0|psi_s> + 1/2 <dn|v|dn> (spin factor 2
+    of Eq. 11, dn = n^alpha - n^0) when the reference density is stationary, i.e. for the full
+    occupied set of eigenstates without cleaning: dE/dt = 0 follows from i psi' = (H0 + v dn) psi.
+    The split-operator steps of Eq. (10) keep it up to O(dt^2): over the same time span the largest
+    excursion |E(t) - E(0)| falls about four times per halving of dt (dt = 0.02 .. 0.005 over 3 au,
+    the asymptotic range on this grid). A strong kick (alpha = 0.2) makes the Hartree term visible;
+    a wrong sign, factor or time level of u breaks the scaling."""
+    p, v, e, phi = tiny8
+    g = tdh.Grid(p.N, p.box)
+    n_occ = 2
+    rho = phi[0] * phi[1]
+    k = 2.0 * np.pi / p.box * (np.fft.fftfreq(p.N) * p.N)
+    g2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+
+    def energy(a, d):
+        psi = a + d
+        hpsi = np.fft.ifftn(0.5 * g2 * np.fft.fftn(psi, axes=(1, 2, 3)), axes=(1, 2, 3)) + v * psi
+        e_h0 = 2.0 * np.sum((psi.conj() * hpsi).real) * g.dV
+        dn = 2.0 * np.sum(np.abs(psi) ** 2 - np.abs(a) ** 2, axis=0)
+        return e_h0 + 0.5 * np.sum(dn * tdh.coulomb_periodic(dn, g)) * g.dV
+
+    drift = []
+    for dt in (0.02, 0.01, 0.005):
+        pr = tdh.TDHParams(n_steps=int(round(3.0 / dt)), dt=dt, gamma=0.0, alpha=0.2, clean_every=0)
+        es = []
+        tdh.tdh_w_pol(g, v, phi[:n_occ], rho, _det_coeff(n_occ), pr,
+                      observe=lambda n, a, d: es.append(energy(a, d)))
+        a0 = tdh.stochastic_orbitals(_det_coeff(n_occ), phi[:n_occ]).astype(complex)
+        q = tdh.coulomb_periodic(rho, g)
+        d0 = (np.exp(-1j * pr.alpha * q) - 1.0)[None] * a0
+        drift.append(np.max(np.abs(np.array(es) - energy(a0, d0))))
+    assert drift[2] < 1e-7 * abs(energy(a0, d0))
+    assert 3.6 < drift[0] / drift[1] < 4.6 and 3.6 < drift[1] / drift[2] < 4.6
+    # the H0 part alone is not conserved (the Hartree term exchanges energy with it)
+    es_h0 = []
+    tdh.tdh_w_pol(g, v, phi[:n_occ], rho, _det_coeff(n_occ), pr,
+                  observe=lambda n, a, d: es_h0.append(2.0 * np.sum((np.conj(a + d) * (np.fft.ifftn(
+                      0.5 * g2 * np.fft.fftn(a + d, axes=(1, 2, 3)), axes=(1, 2, 3)) + v * (a + d))).real) * g.dV))
+    assert np.max(np.abs(np.array(es_h0) - energy(a0, d0))) > 100 * drift[2]
+
+
+@pytest.mark.parametrize("feedback", [False, True])
+def test_static_casida_limit_equals_dense_rpa_solve(tiny8, feedback):
+    """The static branch of the linear-response route (weights=None, S = 1/Omega) against the
+    paper's W = v + v chi v written out directly on the 8^3 grid: chi0(r, r') =
+    -4 sum_{s,c} phi_s phi_c(r) phi_s phi_c(r') / (eps_c - eps_s) over every occupied x virtual pair
+    of the dense H0, v the Coulomb operator applied to unit vectors, chi = (1 - chi0 v)^-1 chi0
+    (chi = chi0 without Hartree feedback), W^pol rho = v chi v rho."""
+    p, v, e, phi = tiny8
+    g = tdh.Grid(p.N, p.box)
+    n_occ = 2
+    ng = p.N ** 3
+    rho = phi[0] * phi[1]
+    occ = phi[:n_occ].reshape(n_occ, ng)
+    vir = phi[n_occ:].reshape(-1, ng)
+    chi0 = np.zeros((ng, ng))
+    for s_ in range(n_occ):
+        prod = occ[s_][None, :] * vir
+        chi0 -= 4.0 * (prod.T / (e[n_occ:] - e[s_])) @ prod
+    V = np.stack([tdh.coulomb_periodic(np.eye(ng)[r].reshape(rho.shape), g).reshape(-1) for r in range(ng)], axis=1)
+    X0 = chi0 * g.dV
+    q = V @ rho.reshape(-1)
+    dn = np.linalg.solve(np.eye(ng) - X0 @ V, X0 @ q) if feedback else X0 @ q
+    w_ref = (V @ dn).reshape(rho.shape)
+    w = rpa.casida_w_pol(g, e, phi, n_occ, rho, None, None, feedback=feedback)
+    assert rel_err(w, w_ref) < 1e-9
