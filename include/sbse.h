@@ -187,9 +187,13 @@ int sbse_absorption(sbse_ctx *ctx, int axis, int n_terms, double broadening, int
  * returns after the stream has synchronised. It calls no cudaMalloc, cudaFree or allocating
  * library routine: its scratch (n^2 + 2n doubles) is a fixed device array of
  * SBSE_NOALLOC_MAX_N^2 + 2 SBSE_NOALLOC_MAX_N doubles (about 2 MB) that every GPU loading the
- * library holds until the process exits. The first call on a device resolves that array's device
- * address (once per device, on the current device); make that first call before any stream
- * capture. All calls on a device share the array, so calls that overlap on the GPU race; the
+ * library holds until the process exits. Each call looks up that array's device address on the
+ * current device (cudaGetSymbolAddress). The array is reserved when the library's device code is
+ * loaded on a device, which under CUDA's default lazy loading is the first call there: a caller
+ * whose memory pool will take the whole GPU should make one call (or set
+ * CUDA_MODULE_LOADING=EAGER) before the pool reserves it, else that first call can fail with CUDA.
+ * Make that first call before any stream capture. Every call synchronises `stream` before it
+ * returns. All calls on a device share the array, so calls that overlap on the GPU race; the
  * array keeps the last call's contents, and nothing in it needs to start at zero.
  * Errors: INVALID_ARG (null pointer, k outside 1..n), SHAPE (n > SBSE_NOALLOC_MAX_N), CUDA;
  * the message is available from sbse_last_error(NULL). */

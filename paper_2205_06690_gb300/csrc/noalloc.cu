@@ -8,7 +8,6 @@
 // loads the library and is held until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "kernels.h"
@@ -27,34 +26,18 @@ constexpr size_t kScratchDoubles = (size_t)kMaxN * kMaxN + 2 * (size_t)kMaxN;
 // only a stand-in for the symbol: the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) double g_eig_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_setup_mutex;
-
-// Once per device, with that device current: resolve the device address of the scratch array.
+// With the calling thread's current device: the device address of the scratch array. It is looked
+// up on every call (cheap once the module is loaded): an address cached per device index would go
+// stale after cudaDeviceReset or differ for another context on the same device.
 int scratch_for_current_device(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    sbse::set_thread_error(std::string("cudaGetDevice failed: ") + cudaGetErrorString(e));
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_eig_scratch);
+  if (e != cudaSuccess || !p) {
+    sbse::set_thread_error(std::string("cudaGetSymbolAddress of the eigensolver scratch failed: ") +
+                           cudaGetErrorString(e));
     return SBSE_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) {
-    sbse::set_thread_error("device index beyond the supported range");
-    return SBSE_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_eig_scratch);
-    if (e != cudaSuccess || !p) {
-      sbse::set_thread_error(std::string("cudaGetSymbolAddress of the eigensolver scratch failed: ") +
-                             cudaGetErrorString(e));
-      return SBSE_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<double *>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double *>(p);
   return SBSE_OK;
 }
 
