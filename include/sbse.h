@@ -233,6 +233,15 @@ int sbse_get_stream(const sbse_ctx *ctx, void **stream);
  * parameters and options are unchanged, removing the host launch cost per step (which dominates
  * on small grids). Not used while sbse_profile is enabled. Results do not depend on it. */
 #define SBSE_OPT_GRAPH 5
+/* SBSE_OPT_MEM_LIMIT_MB (default 0 = none): device memory, in MiB, that the context may hold in
+ * total (grid tables, orbitals, results and scratch). An allocation that would exceed it fails with
+ * SBSE_ERR_OOM and leaves the context as it was before the failing call. */
+#define SBSE_OPT_MEM_LIMIT_MB 6
+/* SBSE_OPT_WAIT_LIMIT (default 0 = 2^23 polls, about a second): iteration limit of the bounded waits
+ * with which the persistent step kernel (SBSE_OPT_PERSISTENT) waits for the tiles it depends on.
+ * A wait that runs out skips its tile's work, the kernel still ends, and sbse_apply_W returns
+ * SBSE_ERR_DEVICE_TIMEOUT with the context still usable. */
+#define SBSE_OPT_WAIT_LIMIT 7
 int sbse_set_option(sbse_ctx *ctx, int option, int value);
 
 /* Number of CUDA kernel launches the library has issued in this process (all contexts), for

@@ -37,6 +37,8 @@ SBSE_OPT_CHUNK_MB = 2
 SBSE_OPT_PERSISTENT = 3
 SBSE_OPT_TMA_PLANES = 4
 SBSE_OPT_GRAPH = 5
+SBSE_OPT_MEM_LIMIT_MB = 6
+SBSE_OPT_WAIT_LIMIT = 7
 
 _ERR_NAMES = {v: k for k, v in globals().items() if k.startswith("SBSE_ERR_")}
 

@@ -655,9 +655,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
   return v;
 }
 
-// bounded wait for *p >= target (about a second at most); false on timeout
-__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target) {
-  for (unsigned i = 0; i < (1u << 23); ++i) {
+// bounded wait for *p >= target (`limit` polls ~100 ns apart; the default 2^23 is about a second);
+// false on timeout
+__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target, unsigned limit) {
+  for (unsigned i = 0; i < limit; ++i) {
     if (ld_acquire(p) >= target) return true;
     __nanosleep(100);
   }
@@ -681,14 +682,14 @@ __global__ void __launch_bounds__(kPPB<T, N> * N)
       const int4 it = (i < (unsigned)q.n_items) ? q.items[i] : make_int4(-1, 0, 0, 0);
       bool ok = true;
       if (it.x == SI_A_Z) {
-        ok = wait_geq(q.a_fwd + it.y, tgt);
+        ok = wait_geq(q.a_fwd + it.y, tgt, q.wait_limit);
       } else if (it.x == SI_A_INV) {
-        ok = wait_geq(q.a_z + it.y, tgt);
+        ok = wait_geq(q.a_z + it.y, tgt, q.wait_limit);
       } else if (it.x == SI_P_Z) {
-        ok = wait_geq(q.p_fwd + it.y, tgt);
+        ok = wait_geq(q.p_fwd + it.y, tgt, q.wait_limit);
       } else if (it.x == SI_P_INV) {
-        ok = wait_geq(q.a_inv, (q.epoch + 1) * (unsigned)(L * G));
-        for (int l = 0; l < L && ok; ++l) ok = wait_geq(q.p_z + it.y * L + l, tgt);
+        ok = wait_geq(q.a_inv, (q.epoch + 1) * (unsigned)(L * G), q.wait_limit);
+        for (int l = 0; l < L && ok; ++l) ok = wait_geq(q.p_z + it.y * L + l, tgt, q.wait_limit);
       }
       if (!ok) atomicExch(q.err, 1);
       __threadfence();

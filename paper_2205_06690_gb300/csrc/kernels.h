@@ -122,6 +122,7 @@ struct StepQueue {
   unsigned *p_fwd, *p_z;  // per pair orbital
   unsigned epoch;         // launch index: completion targets are (epoch + 1) x tiles
   int *err;               // set when a bounded wait times out
+  unsigned wait_limit;    // iterations of each bounded wait (about 100 ns each)
 };
 template <typename T>
 void launch_step_persistent(const GridTables<T> &g, const XfwdArgs<T> &fa, const XfwdArgs<T> &fp,

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.h"
@@ -88,6 +89,11 @@ struct sbse_ctx {
   // profiling
   bool prof = false;
   PhaseClock clk;
+  // device memory held by the context (dalloc / release) and its limit (SBSE_OPT_MEM_LIMIT_MB; 0: none)
+  std::unordered_map<void *, size_t> held;
+  size_t held_bytes = 0, mem_limit = 0;
+  // iteration limit of the persistent step kernel's waits on other tiles (SBSE_OPT_WAIT_LIMIT)
+  unsigned wait_limit = 1u << 23;
 };
 
 namespace {
@@ -119,27 +125,45 @@ int cuda_fail(sbse_ctx *c, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);  \
   } while (0)
 
+// Every device allocation of a context goes through dalloc / release, which keep the context's
+// total (SBSE_OPT_MEM_LIMIT_MB refuses an allocation that would exceed the limit).
 template <typename X> int dalloc(sbse_ctx *ctx, X **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return SBSE_OK;
+  if (ctx->mem_limit && ctx->held_bytes + bytes > ctx->mem_limit)
+    return fail(ctx, SBSE_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                       " bytes would exceed the context's memory limit of " +
+                                       std::to_string(ctx->mem_limit) + " bytes");
   cudaError_t e = cudaMalloc((void **)p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return fail(ctx, SBSE_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   }
+  ctx->held[(void *)*p] = bytes;
+  ctx->held_bytes += bytes;
   return SBSE_OK;
 }
 
-template <typename X> void dfree(X *&p) {
-  if (p) cudaFree((void *)p);
+void release(sbse_ctx *ctx, void *p) {
+  if (!p) return;
+  auto it = ctx->held.find(p);
+  if (it != ctx->held.end()) {
+    ctx->held_bytes -= it->second;
+    ctx->held.erase(it);
+  }
+  cudaFree(p);
+}
+
+template <typename X> void dfree(sbse_ctx *ctx, X *&p) {
+  release(ctx, (void *)p);
   p = nullptr;
 }
 
 int ensure(sbse_ctx *ctx, int slot, size_t bytes, void **out) {
   DevBuf &b = ctx->ws[slot];
   if (b.cap < bytes) {
-    if (b.p) cudaFree(b.p);
+    release(ctx, b.p);
     b.p = nullptr;
     b.cap = 0;
     int rc = dalloc(ctx, &b.p, bytes);
@@ -152,43 +176,43 @@ int ensure(sbse_ctx *ctx, int slot, size_t bytes, void **out) {
 
 void free_scratch(sbse_ctx *ctx) {
   for (auto &b : ctx->ws) {
-    if (b.p) cudaFree(b.p);
+    release(ctx, b.p);
     b.p = nullptr;
     b.cap = 0;
   }
 }
 
 void free_results(sbse_ctx *ctx) {
-  dfree(ctx->W);
-  dfree(ctx->A);
+  dfree(ctx, ctx->W);
+  dfree(ctx, ctx->A);
   ctx->have.clear();
   ctx->have_A = false;
 }
 
 void free_orbitals(sbse_ctx *ctx) {
-  dfree(ctx->phi64);
-  dfree(ctx->phi32);
-  dfree(ctx->eps_dev);
+  dfree(ctx, ctx->phi64);
+  dfree(ctx, ctx->phi32);
+  dfree(ctx, ctx->eps_dev);
   ctx->eps.clear();
   ctx->n_occ = ctx->n_o = ctx->n_c = ctx->n_states = 0;
   free_results(ctx);
 }
 
-template <typename T> void free_tables(GridTables<T> &g) {
-  dfree(g.pv_dt);
-  dfree(g.pv_half);
-  dfree(g.tw);
-  dfree(g.kin);
-  dfree(g.k2);
-  dfree(g.v_loc);
+template <typename T> void free_tables(sbse_ctx *ctx, GridTables<T> &g) {
+  dfree(ctx, g.pv_dt);
+  dfree(ctx, g.pv_half);
+  dfree(ctx, g.tw);
+  dfree(ctx, g.kin);
+  dfree(ctx, g.k2);
+  dfree(ctx, g.v_loc);
   g = GridTables<T>{};
 }
 
 void free_grid(sbse_ctx *ctx) {
   free_orbitals(ctx);
-  free_tables(ctx->g32);
-  free_tables(ctx->g64);
-  dfree(ctx->v64);
+  free_tables(ctx, ctx->g32);
+  free_tables(ctx, ctx->g64);
+  dfree(ctx, ctx->v64);
   ctx->N = 0;
   ctx->ng = 0;
   ctx->kin_dt = -1.0;
@@ -578,6 +602,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     sq.p_fwd = sq.a_inv + 1;
     sq.p_z = sq.p_fwd + (size_t)P * L;
     sq.err = ctx->flag;
+    sq.wait_limit = ctx->wait_limit;
     step_grid = step_resident_blocks<T>(ctx->N);
     if (step_grid <= 0) return fail(ctx, SBSE_ERR_CUDA, "persistent step kernel cannot be resident");
   }
@@ -704,7 +729,8 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       (unsigned long long)(uintptr_t)g.pv_dt, (unsigned long long)(uintptr_t)g.pv_half, (unsigned long long)P,
       (unsigned long long)L, (unsigned long long)Nt, (unsigned long long)M, (unsigned long long)p->feedback,
       (unsigned long long)chunk_pairs, (unsigned long long)persistent, (unsigned long long)sizeof(T),
-      (unsigned long long)(uintptr_t)sq.items, (unsigned long long)(uintptr_t)sq.claim};
+      (unsigned long long)(uintptr_t)sq.items, (unsigned long long)(uintptr_t)sq.claim,
+      (unsigned long long)sq.wait_limit};
   for (double v : {p->dt, p->gamma, p->alpha, ctx->dV}) {
     unsigned long long b;
     memcpy(&b, &v, sizeof b);
@@ -957,7 +983,7 @@ void sbse_destroy(sbse_ctx *ctx) {
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   free_grid(ctx);
   free_scratch(ctx);
-  dfree(ctx->flag);
+  dfree(ctx, ctx->flag);
   for (auto e : ctx->clk.ev) cudaEventDestroy(e);
   if (ctx->aux) cudaStreamSynchronize(ctx->aux);
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
@@ -1266,6 +1292,16 @@ int sbse_set_option(sbse_ctx *ctx, int option, int value) {
   }
   if (option == SBSE_OPT_GRAPH) {
     ctx->use_graph = value != 0;
+    return SBSE_OK;
+  }
+  if (option == SBSE_OPT_MEM_LIMIT_MB) {
+    if (value < 0) return fail(ctx, SBSE_ERR_INVALID_ARG, "memory limit must be >= 0");
+    ctx->mem_limit = (size_t)value << 20;
+    return SBSE_OK;
+  }
+  if (option == SBSE_OPT_WAIT_LIMIT) {
+    if (value < 0) return fail(ctx, SBSE_ERR_INVALID_ARG, "wait limit must be >= 0");
+    ctx->wait_limit = value == 0 ? (1u << 23) : (unsigned)value;
     return SBSE_OK;
   }
   if (option == SBSE_OPT_CHUNK_MB) {
