@@ -178,6 +178,25 @@ int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs);
 int sbse_absorption(sbse_ctx *ctx, int axis, int n_terms, double broadening, int n_omega,
                     const double *omega, double *sigma, double *residues);
 
+/* Finite-box correction W(k -> 0) (Sec. III, paragraph before the algorithm summary): the scissor
+ * shift is lowered by W(k -> 0) = eps_eff^-1 v_bndry, with v_bndry the average Kohn-Sham potential
+ * on the box boundary of a run and eps_eff^-1 fitted so that the spectra of runs in boxes of
+ * several sizes overlap.
+ * sbse_boundary_potential: v_bndry of the context's system, FP64 on the device. Reading: the model's
+ * Kohn-Sham potential is V_loc - mean(V_loc) + v n0, n0 = 2 sum_{s <= N_occ} |phi_s|^2, v the
+ * periodic Coulomb operator with G = 0 dropped; the boundary is the grid points with ix, iy or
+ * iz = 0, averaged with equal weights. v_bndry: host out, Ha. Requires sbse_set_orbitals.
+ * Errors: INVALID_ARG, NOT_READY, OOM, NUMERIC, CUDA. */
+int sbse_boundary_potential(sbse_ctx *ctx, double *v_bndry);
+/* sbse_fit_inverse_dielectric (host only, no context): E is n_box x k (row-major, box-major) lowest
+ * excitons of the runs, v their v_bndry; returns in *eps_inv the least-squares s minimising
+ * sum_{b,j} (E[b,j] - s v[b] - mean_b'(E[b',j] - s v[b']))^2. Errors: INVALID_ARG (n_box < 2, k < 1,
+ * null arrays, all v equal); message from sbse_last_error(NULL). */
+int sbse_fit_inverse_dielectric(int n_box, int k, const double *E, const double *v, double *eps_inv);
+/* Replace the scissor shift Delta of Eq. (9) (e.g. by Delta - eps_eff^-1 v_bndry) without touching
+ * orbitals or W; A must be built again. Errors: INVALID_ARG, NOT_READY, NUMERIC. */
+int sbse_set_scissor(sbse_ctx *ctx, double scissor);
+
 /* Allocation-free variant of sbse_spectrum, for callers that cannot allocate device memory (for
  * example a host framework whose memory pool has reserved the whole GPU, or code that must not
  * trigger an allocation once it runs). The paper has no counterpart: it is an interface addition.

@@ -103,6 +103,9 @@ def load() -> C.CDLL:
         "sbse_set_option": (i, [vp, i, i]),
         "sbse_spectrum_noalloc": (i, [vp, i, i, vp, vp]),
         "sbse_phase_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
+        "sbse_boundary_potential": (i, [vp, dp]),
+        "sbse_fit_inverse_dielectric": (i, [i, i, dp, dp, dp]),
+        "sbse_set_scissor": (i, [vp, d]),
     }
     fp = C.POINTER(C.c_float)
     sig.update({
@@ -279,6 +282,27 @@ def sbse_spectrum_noalloc(a_dev: int, n: int, k: int, evals_dev: int, stream: in
     """Allocation-free eigenvalues: device pointers in and out (see include/sbse.h)."""
     _check(None, load().sbse_spectrum_noalloc(C.c_void_p(a_dev), n, k, C.c_void_p(evals_dev),
                                               C.c_void_p(stream)))
+
+
+def sbse_boundary_potential(ctx) -> float:
+    """v_bndry of the context's system (finite-box correction, see include/sbse.h)."""
+    v = C.c_double()
+    _check(ctx, load().sbse_boundary_potential(ctx, C.byref(v)))
+    return v.value
+
+
+def sbse_fit_inverse_dielectric(E, v) -> float:
+    """eps_eff^-1 from the exciton lists E (n_box x k) and boundary potentials v (n_box)."""
+    Ea = _f64(np.asarray(E, dtype=np.float64))
+    va = _f64(np.asarray(v, dtype=np.float64))
+    s = C.c_double()
+    _check(None, load().sbse_fit_inverse_dielectric(Ea.shape[0], Ea.shape[1], _dptr(Ea), _dptr(va),
+                                                     C.byref(s)))
+    return s.value
+
+
+def sbse_set_scissor(ctx, scissor: float) -> None:
+    _check(ctx, load().sbse_set_scissor(ctx, C.c_double(scissor)))
 
 
 def sbse_profile(ctx, enable: bool) -> None:

@@ -190,6 +190,13 @@ size_t umma_update_phi_bytes(long long ng, int n_occ);
 size_t umma_update_o_bytes(int n_cols, int n_occ);
 void umma_prepare_update_phi(const float *phi, int n_occ, long long ng, uint8_t *phi_can, cudaStream_t s);
 
+// ---- finite-box correction W(k -> 0) (finite_box.cu)
+// n0 = 2 sum_s phi_s^2 over n_occ FP64 rows of ng points
+void launch_ground_density(const double *phi, int n_occ, long long ng, double *n0, cudaStream_t s);
+// sums[0] = sum of v over the grid, sums[1] = sum of v + u over the boundary points (ix, iy or
+// iz = 0); work: 2 x 256 doubles
+void launch_box_sums(const double *v, const double *u, int N, double *work, double *sums, cudaStream_t s);
+
 // ---- absorption spectrum by a Chebyshev expansion of A (spectrum.cu)
 struct SpectrumBufs {
   double *f0, *cw, *v[3], *prod, *R, *D, *omega, *sigma;

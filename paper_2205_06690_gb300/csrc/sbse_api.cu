@@ -100,7 +100,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -1239,6 +1239,67 @@ int sbse_spectrum(sbse_ctx *ctx, int k, double *evals, double *evecs) {
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < k; ++i)
     if (!isfinite(evals[i])) return fail(ctx, SBSE_ERR_NUMERIC, "eigenvalue is not finite");
+  return SBSE_OK;
+}
+
+int sbse_boundary_potential(sbse_ctx *ctx, double *v_bndry) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!v_bndry) return fail(ctx, SBSE_ERR_INVALID_ARG, "v_bndry missing");
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  CK(cudaSetDevice(ctx->device));
+  const long long ng = ctx->ng;
+  cudaStream_t st = ctx->stream;
+  void *vp;
+  int rc;
+  // n0 and u (ng each), the block partial sums and the two totals
+  if ((rc = ensure(ctx, WS_FBOX, (2 * (size_t)ng + 2 * 256 + 2) * sizeof(double), &vp))) return rc;
+  double *n0 = (double *)vp, *u = n0 + ng, *part = u + ng, *sums = part + 2 * 256;
+  if ((rc = ensure(ctx, WS_PW, (size_t)ng * sizeof(C2<double>), &vp))) return rc;
+  launch_ground_density(ctx->phi64, ctx->n_occ, ng, n0, st);
+  if ((rc = poisson<double>(ctx, ctx->g64, n0, 1, (C2<double> *)vp, u, nullptr, 0.0, nullptr, 0.0))) return rc;
+  launch_box_sums(ctx->v64, u, ctx->N, part, sums, st);
+  CHECK_LAUNCH("boundary potential");
+  double h[2];
+  CK(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double nb = 3.0 * ctx->N * (double)ctx->N - 3.0 * ctx->N + 1.0;
+  *v_bndry = h[1] / nb - h[0] / (double)ng;
+  if (!isfinite(*v_bndry)) return fail(ctx, SBSE_ERR_NUMERIC, "boundary potential is not finite");
+  return SBSE_OK;
+}
+
+int sbse_fit_inverse_dielectric(int n_box, int k, const double *E, const double *v, double *eps_inv) {
+  if (n_box < 2 || k < 1 || !E || !v || !eps_inv) {
+    sbse::set_thread_error("need n_box >= 2, k >= 1 and non-null E, v, eps_inv");
+    return SBSE_ERR_INVALID_ARG;
+  }
+  double vbar = 0.0;
+  for (int b = 0; b < n_box; ++b) vbar += v[b];
+  vbar /= n_box;
+  double num = 0.0, den = 0.0;
+  for (int b = 0; b < n_box; ++b) den += (v[b] - vbar) * (v[b] - vbar);
+  for (int j = 0; j < k; ++j) {
+    double ebar = 0.0;
+    for (int b = 0; b < n_box; ++b) ebar += E[(long long)b * k + j];
+    ebar /= n_box;
+    for (int b = 0; b < n_box; ++b) num += (E[(long long)b * k + j] - ebar) * (v[b] - vbar);
+  }
+  if (!(den > 0.0)) {
+    sbse::set_thread_error("the boundary potentials of the boxes must differ");
+    return SBSE_ERR_INVALID_ARG;
+  }
+  *eps_inv = num / (k * den);
+  return SBSE_OK;
+}
+
+int sbse_set_scissor(sbse_ctx *ctx, double scissor) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!isfinite(scissor)) return fail(ctx, SBSE_ERR_NUMERIC, "scissor is not finite");
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  ctx->scissor = scissor;
+  ctx->have_A = false;
   return SBSE_OK;
 }
 

@@ -10,6 +10,7 @@ from .model_system import (  # noqa: F401
     ModelSystem,
     PRESETS,
     batch_presets,
+    box_sweep_presets,
     dense_eigensystem,
     gaussian_wells,
     local_potential,

@@ -49,6 +49,9 @@ class Preset:
     clean_every: int = 10
     scissor: float = 0.5
     n_exc: int = 4
+    # box edge the wells are drawn for (None: this box); the wells are then centred in this box, so
+    # that one molecule can be placed in boxes of several sizes (the box-size sweep of Sec. III)
+    well_box: float | None = None
 
     @property
     def n_pairs(self) -> int:
@@ -82,6 +85,27 @@ def batch_presets(first_seed: int = 100, count: int = 64):
         out.append(Preset(f"batch{s}", N=N, box=0.25 * N, n_wells=int(round(2 * n_occ / 3)),
                           seed=s, n_occ=n_occ, n_o=4, n_c=8, n_steps=500, gamma=0.1, n_exc=4))
     return out
+
+
+def box_sweep_presets(base: Preset, boxes, n_steps: int | None = None):
+    """The molecule of `base` (its wells, drawn for base.box) centred in boxes of the given edges at
+    the same grid spacing (N = box / h): the runs of the finite-box correction of Sec. III."""
+    h = base.box / base.N
+    out = []
+    for b in boxes:
+        N = int(round(b / h))
+        out.append(dataclasses.replace(base, name=f"{base.name}_L{b:g}", N=N, box=float(b),
+                                       well_box=base.box,
+                                       n_steps=base.n_steps if n_steps is None else n_steps))
+    return out
+
+
+def preset_wells(p: Preset) -> np.ndarray:
+    """The wells of a preset: drawn for p.well_box (default p.box) and centred in p.box."""
+    wb = p.box if p.well_box is None else p.well_box
+    w = gaussian_wells(p.n_wells, wb, p.seed)
+    w[:, 2:] += 0.5 * (p.box - wb)
+    return w
 
 
 def gaussian_wells(n_wells: int, box: float, seed: int) -> np.ndarray:
@@ -199,14 +223,15 @@ def _cache_path(p: Preset, n_states: int, tol: float):
     root = os.environ.get("SBSE_INPUT_CACHE")
     if not root:
         return None
-    key = f"{p.N}-{p.box}-{p.n_wells}-{p.seed}-{n_states}-{tol}-{'chfsi' if _use_chfsi(p.N) else 'lobpcg'}"
+    key = (f"{p.N}-{p.box}-{p.n_wells}-{p.seed}-{n_states}-{tol}-{'chfsi' if _use_chfsi(p.N) else 'lobpcg'}"
+           f"-{p.well_box}")
     return os.path.join(root, "sys_" + hashlib.sha1(key.encode()).hexdigest()[:16] + ".npz")
 
 
 def make_system(p: Preset, n_states: int | None = None, tol: float = 1e-6) -> ModelSystem:
     """Build V_loc and the lowest n_states (default N_occ + n_c) orbitals of H0."""
     n_states = p.n_occ + p.n_c if n_states is None else n_states
-    wells = gaussian_wells(p.n_wells, p.box, p.seed)
+    wells = preset_wells(p)
     v = local_potential(p.N, p.box, wells)
     dV = (p.box / p.N) ** 3
     cache = _cache_path(p, n_states, tol)
@@ -234,7 +259,7 @@ def make_system(p: Preset, n_states: int | None = None, tol: float = 1e-6) -> Mo
 
 def dense_eigensystem(p: Preset):
     """All eigenpairs of the dense H0 (small grids only); orbitals normalised with dV."""
-    wells = gaussian_wells(p.n_wells, p.box, p.seed)
+    wells = preset_wells(p)
     v = local_potential(p.N, p.box, wells)
     e, vec = np.linalg.eigh(_dense_h0(p.N, p.box, v))
     dV = (p.box / p.N) ** 3
@@ -243,5 +268,6 @@ def dense_eigensystem(p: Preset):
     return v, e, (vec.T / np.sqrt(dV)).reshape(-1, p.N, p.N, p.N)
 
 
-__all__ = ["Preset", "PRESETS", "ModelSystem", "preset", "batch_presets", "gaussian_wells",
+__all__ = ["Preset", "PRESETS", "ModelSystem", "preset", "batch_presets", "box_sweep_presets",
+           "preset_wells", "gaussian_wells",
            "local_potential", "make_system", "dense_eigensystem"]
