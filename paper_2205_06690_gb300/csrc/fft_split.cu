@@ -246,24 +246,26 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_kin2(GView<flo
   preop_plane<N, PAIR>(g, a, item, off, S);
   __syncthreads();
   const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
-  // the x operator on row p (in place), then the y operator on column p (stored to global): one
-  // copy of the code for both axes (addressed through generic pointers), which halves the
-  // instruction footprint of the fully unrolled transforms
-  C *const out = a.out + item * g.ng + off + p;
-#pragma unroll 1
-  for (int axis = 0; axis < 2; ++axis) {
-    const C *src = axis == 0 ? S + p * LD : S + p;
-    const int sst = axis == 0 ? 1 : LD;
+  {  // x operator on row p, in place
     C v[H];
+    C *row = S + p * LD;
 #pragma unroll
-    for (int m = 0; m < H; ++m) v[m] = src[(2 * m + s) * sst];
+    for (int m = 0; m < H; ++m) v[m] = row[2 * m + s];
     kin_roundtrip<N>(v, s, tab);
-    C *dst = axis == 0 ? S + p * LD : out;
-    const int dstr = axis == 0 ? 1 : N;
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < H; ++m) dst[(2 * m + s) * dstr] = v[m];
-    if (axis == 0) __syncthreads();
+    for (int m = 0; m < H; ++m) row[2 * m + s] = v[m];
+  }
+  __syncthreads();
+  {  // y operator on column p, stored to global
+    C v[H];
+    const C *col = S + p;
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = col[(2 * m + s) * LD];
+    kin_roundtrip<N>(v, s, tab);
+    C *out = a.out + item * g.ng + off + p;
+#pragma unroll
+    for (int m = 0; m < H; ++m) out[(2 * m + s) * N] = v[m];
   }
 }
 
