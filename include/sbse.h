@@ -53,6 +53,7 @@ extern "C" {
 /* terms of Eq. (1) included by sbse_build_A (the diagonal eps_a - eps_i + Delta is always in) */
 #define SBSE_EXCHANGE 1u /* + 2 (ia|jb) */
 #define SBSE_DIRECT 2u   /* - (phi_a phi_b | W | phi_i phi_j) */
+#define SBSE_DIRECT_PARTIAL 4u /* the direct term from the pairs that have W; the others count as zero */
 
 typedef struct sbse_ctx sbse_ctx;
 
@@ -146,7 +147,11 @@ int sbse_get_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, double 
  * with (ia|jb) = sum_r phi_i phi_a (r) [v phi_j phi_b](r) h^3 (exchange element after Eq. 1) and
  * (phi_a phi_b|W|phi_i phi_j) = sum_r phi_a phi_b (r) W_ij(r) h^3 (direct element), W_ji = W_ij.
  * Index ia = i * n_c + a. terms: bitwise OR of SBSE_EXCHANGE and SBSE_DIRECT (0 gives the
- * diagonal only). SBSE_DIRECT requires W for all n_o (n_o + 1) / 2 pairs.
+ * diagonal only). SBSE_DIRECT requires W for all n_o (n_o + 1) / 2 pairs; SBSE_DIRECT_PARTIAL
+ * takes W = 0 for the pairs without one (screened-out pairs of a localized window, see
+ * sbse_localize_occupied). After sbse_localize_occupied the diagonal term is
+ * delta_ab (eps_a delta_ij - F_ij) + Delta delta_ij delta_ab with F the occupied block of H0 in the
+ * rotated window.
  * a_out: optional host (n_o n_c)^2 doubles, row-major; NULL keeps A on the device.
  * Errors: INVALID_ARG, NOT_READY, OOM, CUDA. */
 int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out);
@@ -193,6 +198,20 @@ int sbse_boundary_potential(sbse_ctx *ctx, double *v_bndry);
  * sum_{b,j} (E[b,j] - s v[b] - mean_b'(E[b',j] - s v[b']))^2. Errors: INVALID_ARG (n_box < 2, k < 1,
  * null arrays, all v equal); message from sbse_last_error(NULL). */
 int sbse_fit_inverse_dielectric(int n_box, int k, const double *E, const double *v, double *eps_inv);
+/* Localized occupied window (Forward perspective: localized occupied orbitals reduce the number of
+ * (i, j) pairs whose W_ij is needed). sbse_localize_occupied rotates the n_o window orbitals,
+ * phi'_k = sum_i U_ik phi_i with U orthogonal, to maximise the periodic localization functional
+ * sum_{alpha = x,y,z} sum_k |Z'_alpha,kk|^2, Z_alpha,ij = sum_r phi_i phi_j exp(i 2 pi x_alpha / L) h^3
+ * (Jacobi sweeps; at most max_sweeps, stopping when a sweep gains less than tol relative). The
+ * context then works in the rotated window: W, A (with F = U^T diag(eps_o) U on its diagonal term)
+ * and the spectra refer to it; W computed before is dropped. U_out: optional host n_o x n_o,
+ * row-major (U_out[i n_o + k] = U_ik). Errors: INVALID_ARG, NOT_READY, OOM, CUDA.
+ * sbse_pair_weights: w_p = (sum_r (phi_i phi_j)^2 h^3)^1/2 for the n_o (n_o + 1) / 2 window pairs in
+ * the canonical order (0,0), (0,1), .., (1,1), ..: the norms by which pairs are screened before
+ * sbse_apply_W. w_out: host out. Errors: INVALID_ARG, NOT_READY, OOM, CUDA. */
+int sbse_localize_occupied(sbse_ctx *ctx, int max_sweeps, double tol, double *U_out);
+int sbse_pair_weights(sbse_ctx *ctx, double *w_out);
+
 /* Replace the scissor shift Delta of Eq. (9) (e.g. by Delta - eps_eff^-1 v_bndry) without touching
  * orbitals or W; A must be built again. Errors: INVALID_ARG, NOT_READY, NUMERIC. */
 int sbse_set_scissor(sbse_ctx *ctx, double scissor);

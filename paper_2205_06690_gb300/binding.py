@@ -32,6 +32,7 @@ SBSE_COEFF_GAUSSIAN = 0
 SBSE_COEFF_SIGN = 1
 SBSE_EXCHANGE = 1
 SBSE_DIRECT = 2
+SBSE_DIRECT_PARTIAL = 4
 SBSE_OPT_TENSOR_CORES = 1
 SBSE_OPT_CHUNK_MB = 2
 SBSE_OPT_PERSISTENT = 3
@@ -106,6 +107,8 @@ def load() -> C.CDLL:
         "sbse_boundary_potential": (i, [vp, dp]),
         "sbse_fit_inverse_dielectric": (i, [i, i, dp, dp, dp]),
         "sbse_set_scissor": (i, [vp, d]),
+        "sbse_localize_occupied": (i, [vp, i, d, dp]),
+        "sbse_pair_weights": (i, [vp, dp]),
     }
     fp = C.POINTER(C.c_float)
     sig.update({
@@ -299,6 +302,20 @@ def sbse_fit_inverse_dielectric(E, v) -> float:
     _check(None, load().sbse_fit_inverse_dielectric(Ea.shape[0], Ea.shape[1], _dptr(Ea), _dptr(va),
                                                      C.byref(s)))
     return s.value
+
+
+def sbse_localize_occupied(ctx, n_o: int, max_sweeps: int = 100, tol: float = 1e-12):
+    """Rotate the occupied window to localized orbitals; returns U (n_o x n_o)."""
+    U = np.empty((n_o, n_o))
+    _check(ctx, load().sbse_localize_occupied(ctx, max_sweeps, tol, _dptr(U)))
+    return U
+
+
+def sbse_pair_weights(ctx, n_o: int):
+    """Pair-density norms of the window pairs, canonical order."""
+    w = np.empty(n_o * (n_o + 1) // 2)
+    _check(ctx, load().sbse_pair_weights(ctx, _dptr(w)))
+    return w
 
 
 def sbse_set_scissor(ctx, scissor: float) -> None:

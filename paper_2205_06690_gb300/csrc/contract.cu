@@ -45,15 +45,21 @@ void launch_prod_gemm(const T *F, const int2 *xi, int M, const T *Y, int Nn, lon
 // A[ia][jb] = delta (eps_a - eps_i + Delta) + 2 K[ia][jb] - Dab[a * n_c + b][p(i, j)], with
 // p(i, j) the index of the pair (min(i,j), max(i,j)) in the order (0,0), (0,1), .., (1,1), ..
 // and W_ji = W_ij, so for i > j the direct element is Dab[b * n_c + a][p(j, i)].
-// K or Dab may be null (term switched off).
+// K or Dab may be null (term switched off). With fock_o (a rotated occupied window, Forward
+// perspective) the diagonal term is delta_ab (eps_a delta_ij - F_ij) + Delta delta_ij delta_ab.
 __global__ void k_assemble_A(const double *eps_o, const double *eps_c, int n_o, int n_c,
-                             double scissor, const double *K, const double *Dab, int P, double *A) {
+                             double scissor, const double *K, const double *Dab, int P, double *A,
+                             const double *fock_o) {
   const int n = n_o * n_c;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * n) return;
   const int row = (int)(idx / n), col = (int)(idx % n);
   const int i = row / n_c, a = row % n_c, j = col / n_c, b = col % n_c;
-  double v = (row == col) ? (eps_c[a] - eps_o[i] + scissor) : 0.0;
+  double v;
+  if (fock_o)
+    v = (a == b ? ((i == j ? eps_c[a] + scissor : 0.0) - fock_o[i * n_o + j]) : 0.0);
+  else
+    v = (row == col) ? (eps_c[a] - eps_o[i] + scissor) : 0.0;
   if (K) v += 2.0 * K[idx];
   if (Dab) {
     const int lo = i < j ? i : j, hi = i < j ? j : i;
@@ -65,10 +71,11 @@ __global__ void k_assemble_A(const double *eps_o, const double *eps_c, int n_o, 
 }
 
 void launch_assemble_A(const double *eps_o, const double *eps_c, int n_o, int n_c, double scissor,
-                       const double *K, const double *Dab, int P, double *A, cudaStream_t s) {
+                       const double *K, const double *Dab, int P, double *A, cudaStream_t s,
+                       const double *fock_o) {
   const long long n2 = (long long)(n_o * n_c) * (n_o * n_c);
   k_assemble_A<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(eps_o, eps_c, n_o, n_c, scissor, K, Dab,
-                                                           P, A);
+                                                           P, A, fock_o);
   count_launch(1);
 }
 

@@ -165,8 +165,10 @@ template <typename T> void launch_prod_gemm(const T *F, const int2 *xi, int M, c
                                             long long ng, double scale, double *out, double *work,
                                             size_t work_bytes, cudaStream_t s);
 template <typename T> size_t prod_gemm_work_bytes(int M, int Nn, long long ng);
+// fock_o (n_o x n_o, may be null): the occupied block of H0 in a rotated window, replacing eps_o
 void launch_assemble_A(const double *eps_o, const double *eps_c, int n_o, int n_c, double scissor,
-                       const double *K, const double *Dab, int P, double *A, cudaStream_t s);
+                       const double *K, const double *Dab, int P, double *A, cudaStream_t s,
+                       const double *fock_o = nullptr);
 
 // tensor-core (tcgen05, BF16 split, FP32 accumulate) version of launch_prod_gemm for FP32 inputs;
 // *err (device int) is set when a bounded wait on the tensor cores times out
@@ -196,6 +198,17 @@ void launch_ground_density(const double *phi, int n_occ, long long ng, double *n
 // sums[0] = sum of v over the grid, sums[1] = sum of v + u over the boundary points (ix, iy or
 // iz = 0); work: 2 x 256 doubles
 void launch_box_sums(const double *v, const double *u, int N, double *work, double *sums, cudaStream_t s);
+
+// ---- localized occupied window (localized.cu)
+// cos, sin(2 pi x_alpha / L) for alpha = x, y, z: six fields of N^3 points
+void launch_phase_fields(int N, double *out, cudaStream_t s);
+// out[k] = sum_i U_ik phi[base + i], k < n (n x n row-major U, n <= 96 for the shared copy of U)
+void launch_rotate_rows(const double *phi, int base, int n, const double *U, long long ng, double *out,
+                        cudaStream_t s);
+// out[p] = scale sum_r (phi[pairs[p].x] phi[pairs[p].y])^2; work: pair_norms_work_doubles(n_pairs)
+size_t pair_norms_work_doubles(int n_pairs);
+void launch_pair_norms(const double *phi, const int2 *pairs, int n_pairs, long long ng, double scale,
+                       double *work, double *out, cudaStream_t s);
 
 // ---- absorption spectrum by a Chebyshev expansion of A (spectrum.cu)
 struct SpectrumBufs {

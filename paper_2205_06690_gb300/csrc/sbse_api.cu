@@ -65,6 +65,9 @@ struct sbse_ctx {
   float *phi32 = nullptr;
   std::vector<double> eps;
   double *eps_dev = nullptr;  // eps_o (n_o) then eps_c (n_c)
+  // a rotated (localized) occupied window: the occupied block of H0 in it (n_o x n_o, device)
+  double *fock_o = nullptr;
+  bool localized = false;
   // results
   double *W = nullptr;  // P_all x ng, canonical pair order
   std::vector<char> have;
@@ -100,7 +103,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX, WS_LOC
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -190,6 +193,8 @@ void free_results(sbse_ctx *ctx) {
 }
 
 void free_orbitals(sbse_ctx *ctx) {
+  dfree(ctx, ctx->fock_o);
+  ctx->localized = false;
   dfree(ctx, ctx->phi64);
   dfree(ctx, ctx->phi32);
   dfree(ctx, ctx->eps_dev);
@@ -866,9 +871,14 @@ template <typename T> int run_build_A(sbse_ctx *ctx, unsigned terms) {
     CHECK_LAUNCH("exchange");
     CK(cudaStreamSynchronize(st));
   }
-  if (terms & SBSE_DIRECT) {
-    for (int q = 0; q < P; ++q)
-      if (!ctx->have[q]) return fail(ctx, SBSE_ERR_NOT_READY, "W missing for some pairs: call sbse_apply_W for all n_o(n_o+1)/2 pairs first");
+  if (terms & (SBSE_DIRECT | SBSE_DIRECT_PARTIAL)) {
+    for (int q = 0; q < P; ++q) {
+      if (ctx->have[q]) continue;
+      if (!(terms & SBSE_DIRECT_PARTIAL))
+        return fail(ctx, SBSE_ERR_NOT_READY, "W missing for some pairs: call sbse_apply_W for all n_o(n_o+1)/2 pairs first");
+      // a screened-out pair: its W is taken as zero
+      CK(cudaMemsetAsync(ctx->W + (long long)q * ng, 0, ng * sizeof(double), st));
+    }
     const int Mab = n_c * n_c;
     std::vector<int2> xi(Mab);
     for (int m = 0; m < Mab; ++m) xi[m] = make_int2(ctx->n_occ + m / n_c, ctx->n_occ + m % n_c);
@@ -891,7 +901,8 @@ template <typename T> int run_build_A(sbse_ctx *ctx, unsigned terms) {
   clk_end(ctx, c3);
   size_t c4 = 0;
   clk_begin(ctx, 4, &c4);
-  launch_assemble_A(ctx->eps_dev, ctx->eps_dev + n_o, n_o, n_c, ctx->scissor, K, Dab, P, ctx->A, st);
+  launch_assemble_A(ctx->eps_dev, ctx->eps_dev + n_o, n_o, n_c, ctx->scissor, K, Dab, P, ctx->A, st,
+                    ctx->localized ? ctx->fock_o : nullptr);
   CHECK_LAUNCH("assemble_A");
   clk_end(ctx, c4);
   CK(cudaStreamSynchronize(st));
@@ -1190,7 +1201,8 @@ int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out) {
   if (!ctx) return SBSE_ERR_INVALID_ARG;
   ctx->err.clear();
   if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
-  if (terms & ~(SBSE_EXCHANGE | SBSE_DIRECT)) return fail(ctx, SBSE_ERR_INVALID_ARG, "unknown terms bits");
+  if (terms & ~(SBSE_EXCHANGE | SBSE_DIRECT | SBSE_DIRECT_PARTIAL))
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "unknown terms bits");
   CK(cudaSetDevice(ctx->device));
   const int rc = ctx->precision == SBSE_FP64 ? run_build_A<double>(ctx, terms)
                                              : run_build_A<float>(ctx, terms);
@@ -1290,6 +1302,144 @@ int sbse_fit_inverse_dielectric(int n_box, int k, const double *E, const double 
     return SBSE_ERR_INVALID_ARG;
   }
   *eps_inv = num / (k * den);
+  return SBSE_OK;
+}
+
+int sbse_localize_occupied(sbse_ctx *ctx, int max_sweeps, double tol, double *U_out) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (max_sweeps < 1 || !(tol >= 0.0)) return fail(ctx, SBSE_ERR_INVALID_ARG, "need max_sweeps >= 1, tol >= 0");
+  CK(cudaSetDevice(ctx->device));
+  const int n = ctx->n_o, P = n * (n + 1) / 2, base = ctx->n_occ - n;
+  const long long ng = ctx->ng;
+  cudaStream_t st = ctx->stream;
+  void *vp;
+  int rc;
+  // the spread matrices Z_alpha,ij = dV sum_r phi_i phi_j exp(i 2 pi x_alpha / L), i <= j: a grid sum
+  // of the window's pair products against the six fields cos, sin(2 pi x_alpha / L)
+  if ((rc = ensure(ctx, WS_LOC, (6 * (size_t)ng + (size_t)n * ng + 6 * (size_t)P + 2 * (size_t)n * n) * sizeof(double), &vp)))
+    return rc;
+  double *fields = (double *)vp, *rot = fields + 6 * ng, *zout = rot + (long long)n * ng, *Udev = zout + 6 * P;
+  std::vector<int2> xi(P);
+  for (int i = 0, p = 0; i < n; ++i)
+    for (int j = i; j < n; ++j, ++p) xi[p] = make_int2(base + i, base + j);
+  if ((rc = ensure(ctx, WS_IDX, (size_t)P * sizeof(int2), &vp))) return rc;
+  int2 *xi_dev = (int2 *)vp;
+  CK(cudaMemcpyAsync(xi_dev, xi.data(), P * sizeof(int2), cudaMemcpyHostToDevice, st));
+  launch_phase_fields(ctx->N, fields, st);
+  const size_t gw = prod_gemm_work_bytes<double>(P, 6, ng);
+  if ((rc = ensure(ctx, WS_GEMM, gw, &vp))) return rc;
+  launch_prod_gemm<double>(ctx->phi64, xi_dev, P, fields, 6, ng, ctx->dV, zout, (double *)vp, gw, st);
+  CHECK_LAUNCH("spread matrices");
+  std::vector<double> zh(6 * (size_t)P);
+  CK(cudaMemcpyAsync(zh.data(), zout, zh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // Jacobi maximisation of sum_alpha sum_k |Z_alpha,kk|^2 over orthogonal rotations (host)
+  std::vector<double> zr(3 * (size_t)n * n), zi(3 * (size_t)n * n), U((size_t)n * n, 0.0);
+  for (int i = 0, p = 0; i < n; ++i)
+    for (int j = i; j < n; ++j, ++p)
+      for (int a = 0; a < 3; ++a) {
+        zr[((size_t)a * n + i) * n + j] = zr[((size_t)a * n + j) * n + i] = zh[(size_t)p * 6 + 2 * a];
+        zi[((size_t)a * n + i) * n + j] = zi[((size_t)a * n + j) * n + i] = zh[(size_t)p * 6 + 2 * a + 1];
+      }
+  for (int i = 0; i < n; ++i) U[(size_t)i * n + i] = 1.0;
+  auto functional = [&]() {
+    double f = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < n; ++k) {
+        const size_t d = ((size_t)a * n + k) * n + k;
+        f += zr[d] * zr[d] + zi[d] * zi[d];
+      }
+    return f;
+  };
+  double prev = functional();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int i = 0; i < n - 1; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        double Pv = 0.0, Qv = 0.0, Rv = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const size_t ii = ((size_t)a * n + i) * n + i, jj = ((size_t)a * n + j) * n + j, ij = ((size_t)a * n + i) * n + j;
+          const double ur = 0.5 * (zr[ii] - zr[jj]), ui = 0.5 * (zi[ii] - zi[jj]);
+          Pv += ur * ur + ui * ui;
+          Qv += zr[ij] * zr[ij] + zi[ij] * zi[ij];
+          Rv += ur * zr[ij] + ui * zi[ij];
+        }
+        const double theta = 0.25 * atan2(Rv, 0.5 * (Pv - Qv));
+        if (fabs(theta) < 1e-15) continue;
+        const double c = cos(theta), sn = sin(theta);
+        // new i = c i + s j, new j = -s i + c j: columns, then rows of each Z_alpha, then U
+        for (int a = 0; a < 3; ++a)
+          for (double *z : {zr.data(), zi.data()}) {
+            double *Z = z + (size_t)a * n * n;
+            for (int k = 0; k < n; ++k) {
+              const double zki = Z[(size_t)k * n + i], zkj = Z[(size_t)k * n + j];
+              Z[(size_t)k * n + i] = c * zki + sn * zkj;
+              Z[(size_t)k * n + j] = -sn * zki + c * zkj;
+            }
+            for (int k = 0; k < n; ++k) {
+              const double zik = Z[(size_t)i * n + k], zjk = Z[(size_t)j * n + k];
+              Z[(size_t)i * n + k] = c * zik + sn * zjk;
+              Z[(size_t)j * n + k] = -sn * zik + c * zjk;
+            }
+          }
+        for (int k = 0; k < n; ++k) {
+          const double uki = U[(size_t)k * n + i], ukj = U[(size_t)k * n + j];
+          U[(size_t)k * n + i] = c * uki + sn * ukj;
+          U[(size_t)k * n + j] = -sn * uki + c * ukj;
+        }
+      }
+    const double f = functional();
+    const bool done = f - prev <= tol * std::max(1.0, fabs(f));
+    prev = f;
+    if (done) break;
+  }
+  // rotate the window rows on the device, refresh the FP32 copy; F = U^T diag(eps_o) U
+  std::vector<double> F((size_t)n * n);
+  for (int k = 0; k < n; ++k)
+    for (int l = 0; l < n; ++l) {
+      double v = 0.0;
+      for (int i = 0; i < n; ++i) v += U[(size_t)i * n + k] * ctx->eps[base + i] * U[(size_t)i * n + l];
+      F[(size_t)k * n + l] = v;
+    }
+  if (!ctx->fock_o && (rc = dalloc(ctx, &ctx->fock_o, (size_t)n * n * sizeof(double)))) return rc;
+  CK(cudaMemcpyAsync(Udev, U.data(), U.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->fock_o, F.data(), F.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  launch_rotate_rows(ctx->phi64, base, n, Udev, ng, rot, st);
+  CK(cudaMemcpyAsync(ctx->phi64 + (long long)base * ng, rot, (size_t)n * ng * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_convert<float>(ctx->phi64 + (long long)base * ng, ctx->phi32 + (long long)base * ng, (long long)n * ng, st);
+  CHECK_LAUNCH("rotate window");
+  std::fill(ctx->have.begin(), ctx->have.end(), 0);
+  ctx->have_A = false;
+  ctx->localized = true;
+  if (U_out) std::copy(U.begin(), U.end(), U_out);
+  CK(cudaStreamSynchronize(st));
+  return SBSE_OK;
+}
+
+int sbse_pair_weights(sbse_ctx *ctx, double *w_out) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!w_out) return fail(ctx, SBSE_ERR_INVALID_ARG, "w_out missing");
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  CK(cudaSetDevice(ctx->device));
+  const int n = ctx->n_o, P = n * (n + 1) / 2, base = ctx->n_occ - n;
+  cudaStream_t st = ctx->stream;
+  void *vp;
+  int rc;
+  std::vector<int2> xi(P);
+  for (int i = 0, p = 0; i < n; ++i)
+    for (int j = i; j < n; ++j, ++p) xi[p] = make_int2(base + i, base + j);
+  if ((rc = ensure(ctx, WS_IDX, (size_t)P * sizeof(int2), &vp))) return rc;
+  int2 *xi_dev = (int2 *)vp;
+  CK(cudaMemcpyAsync(xi_dev, xi.data(), P * sizeof(int2), cudaMemcpyHostToDevice, st));
+  if ((rc = ensure(ctx, WS_LOC, (pair_norms_work_doubles(P) + P) * sizeof(double), &vp))) return rc;
+  double *work = (double *)vp, *out = work + pair_norms_work_doubles(P);
+  launch_pair_norms(ctx->phi64, xi_dev, P, ctx->ng, ctx->dV, work, out, st);
+  CHECK_LAUNCH("pair norms");
+  CK(cudaMemcpyAsync(w_out, out, P * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int p = 0; p < P; ++p) w_out[p] = sqrt(w_out[p]);
   return SBSE_OK;
 }
 
