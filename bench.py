@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--pairs-per-step", type=int, default=None,
                     help="pairs per benchmark step (default: all up to 64, else one eighth)")
     ap.add_argument("--prof-steps", type=int, default=2)
+    ap.add_argument("--batch-workers", type=int, default=8, help="batch64: systems run at once")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--n-steps", type=int, default=None, help="override the TDH step count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -246,10 +247,83 @@ def block_default(pre) -> int:
     return pre.n_pairs if pre.n_pairs <= 64 else -(-pre.n_pairs // 8)
 
 
+def batch_bench(args):
+    """The batching form: 64 independent Gaussian-well systems of uneven grids ({32,40,48,64,80}^3,
+    h = 0.25 bohr, N_occ = N/2, n_o = 4, n_c = 8, 500 steps), one context each, run concurrently
+    from a pool of host threads; one step = the whole hot path of every system."""
+    import numpy as np
+    import torch
+
+    os.environ.setdefault("SBSE_EIGENSOLVER", "chfsi")  # orbitals of 64 systems: on the GPU
+    import sbse_inputs as si
+    from paper_2205_06690_gb300 import batch
+    from paper_2205_06690_gb300 import binding as B
+    pres = si.batch_presets()
+    t_in = time.perf_counter()
+    items = []
+    for p in pres:
+        s = si.make_system(p)
+        items.append(batch.BatchItem(p.N, p.box, s.v_loc, np.ascontiguousarray(s.phi), np.ascontiguousarray(s.eps),
+                                     p.n_occ, p.n_o, p.n_c, p.scissor, p.n_exc, seed=p.seed))
+    t_in = time.perf_counter() - t_in
+    prm = B.TDHParams(n_s=10, n_steps=args.n_steps or 500, clean_every=10, dt=0.05, gamma=0.1, alpha=1e-4)
+    n_pairs = sum(it.n_o * (it.n_o + 1) // 2 for it in items)
+    bt = batch.Batch(items, B.SBSE_MIXED)
+    for _ in range(args.warmup):
+        bt.run(prm, workers=args.batch_workers, tune=True)
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clk.start()
+    launches0 = B.sbse_kernel_launches()
+    walls = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        res, wall = bt.run(prm, workers=args.batch_workers, tune=True)
+        torch.cuda.synchronize()
+        walls.append(wall)
+    clocks = clk.stop()
+    launches = B.sbse_kernel_launches() - launches0
+    # the same systems one after another (no concurrency), for the gain of the pool
+    torch.cuda.synchronize()
+    _, serial = bt.run(prm, workers=1, tune=True)
+    torch.cuda.synchronize()
+    bt.close()
+    # exciton error of the mixed path against the FP64 GPU path on one system of each grid size
+    check = {}
+    for n in sorted({it.n for it in items}):
+        idx = [i for i, x in enumerate(items) if x.n == n][0]
+        r64, _ = batch.run_batch([items[idx]], prm, precision=B.SBSE_FP64, workers=1, tune=False)
+        check[str(n)] = float(np.max(np.abs(res[idx]["excitons"] - r64[0]["excitons"])) * 27211.386245988)
+    ms_step = 1e3 * statistics.mean(walls)
+    line = {
+        "metric": "W-rho applications/sec (stochastic TDH, all pairs) + A build",
+        "value": n_pairs / (ms_step / 1e3), "unit": "W-applications/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch64: {len(items)} Gaussian-well systems (seeds 100-163), grids "
+                               f"{{32,40,48,64,80}}^3 at h = 0.25 bohr, N_occ = N/2, n_o = 4, n_c = 8, "
+                               f"{n_pairs} pairs in all, L = 10, {prm.n_steps} steps, M = 10",
+                   "step": "the whole hot path (all pairs, A, 4 excitons) of every system, "
+                           f"{args.batch_workers} systems at a time from a thread pool, each time loop "
+                           "replayed as a CUDA graph, per-grid variant from the autotuner",
+                   "timing": "host wall clock between device-wide synchronisations (the systems run on "
+                             "their own streams)"},
+        "clocks": clocks, "gpu_launches": launches,
+        "serial_ms_per_step": 1e3 * serial, "concurrency_gain": serial / (ms_step / 1e3),
+        "autotuned": {f"{k[0]}": v for k, v in batch._TUNED.items()},
+        "exciton_dev_vs_fp64_mev": check, "inputs_s": t_in,
+        "e2e": None, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.oracle_child:
         _oracle_child(args.oracle_child)
+        return
+    if args.workload == "batch64" and args.impl == "ours":
+        batch_bench(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

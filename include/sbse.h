@@ -156,6 +156,16 @@ int sbse_get_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, double 
  * Errors: INVALID_ARG, NOT_READY, OOM, CUDA. */
 int sbse_build_A(sbse_ctx *ctx, unsigned terms, double *a_out);
 
+/* The direct element split by pairs, for one system spread over several GPUs (each rank propagates a
+ * block of pairs; the pairs are independent W applications): sbse_get_direct returns, for n_pairs
+ * pairs (i, j) with W available, the columns D[ab][k] = sum_r phi_a phi_b (r) W_{i_k j_k}(r) h^3,
+ * ab = a n_c + b (all n_c^2 products), as a host n_c^2 x n_pairs row-major array; sbse_set_direct
+ * takes the n_c^2 x n_o (n_o + 1) / 2 array of every pair in the canonical order (the ranks'
+ * columns gathered) and makes the next sbse_build_A with SBSE_DIRECT use it instead of W (until W
+ * changes). Errors: INVALID_ARG, NOT_READY (W missing), NUMERIC, OOM, CUDA. */
+int sbse_get_direct(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, double *dab);
+int sbse_set_direct(sbse_ctx *ctx, const double *dab);
+
 /* Lowest k eigenvalues of A (Eq. 1; the exciton energies, Ha), ascending, by an FP64
  * Householder tridiagonalisation and Sturm bisection on the device.
  * evals: host, k doubles. evecs: optional host (n_o n_c) x k doubles, row-major (component ia of

@@ -109,6 +109,8 @@ def load() -> C.CDLL:
         "sbse_set_scissor": (i, [vp, d]),
         "sbse_localize_occupied": (i, [vp, i, d, dp]),
         "sbse_pair_weights": (i, [vp, dp]),
+        "sbse_get_direct": (i, [vp, i, ip, ip, dp]),
+        "sbse_set_direct": (i, [vp, dp]),
     }
     fp = C.POINTER(C.c_float)
     sig.update({
@@ -316,6 +318,20 @@ def sbse_pair_weights(ctx, n_o: int):
     w = np.empty(n_o * (n_o + 1) // 2)
     _check(ctx, load().sbse_pair_weights(ctx, _dptr(w)))
     return w
+
+
+def sbse_get_direct(ctx, pairs, n_c: int):
+    """Direct-element columns of `pairs` (n_c^2 x len(pairs)), see include/sbse.h."""
+    pi = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
+    pj = np.ascontiguousarray([p[1] for p in pairs], dtype=np.int32)
+    out = np.empty((n_c * n_c, len(pairs)))
+    ip = C.POINTER(C.c_int)
+    _check(ctx, load().sbse_get_direct(ctx, len(pairs), pi.ctypes.data_as(ip), pj.ctypes.data_as(ip), _dptr(out)))
+    return out
+
+
+def sbse_set_direct(ctx, dab) -> None:
+    _check(ctx, load().sbse_set_direct(ctx, _dptr(_f64(dab))))
 
 
 def sbse_set_scissor(ctx, scissor: float) -> None:

@@ -73,6 +73,7 @@ struct sbse_ctx {
   std::vector<char> have;
   double *A = nullptr;
   bool have_A = false;
+  bool dab_given = false;  // the direct term's D columns were set by sbse_set_direct (in WS_DAB)
   // scratch
   DevBuf ws[24];
   int *flag = nullptr;
@@ -103,7 +104,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX, WS_LOC
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX, WS_LOC, WS_DBLK
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -190,6 +191,7 @@ void free_results(sbse_ctx *ctx) {
   dfree(ctx, ctx->A);
   ctx->have.clear();
   ctx->have_A = false;
+  ctx->dab_given = false;
 }
 
 void free_orbitals(sbse_ctx *ctx) {
@@ -871,7 +873,11 @@ template <typename T> int run_build_A(sbse_ctx *ctx, unsigned terms) {
     CHECK_LAUNCH("exchange");
     CK(cudaStreamSynchronize(st));
   }
-  if (terms & (SBSE_DIRECT | SBSE_DIRECT_PARTIAL)) {
+  if ((terms & SBSE_DIRECT) && ctx->dab_given) {
+    // D columns of every pair set by sbse_set_direct (e.g. gathered from other ranks)
+    if ((rc = ensure(ctx, WS_DAB, (size_t)n_c * n_c * P * sizeof(double), &vp))) return rc;
+    Dab = (double *)vp;
+  } else if (terms & (SBSE_DIRECT | SBSE_DIRECT_PARTIAL)) {
     for (int q = 0; q < P; ++q) {
       if (ctx->have[q]) continue;
       if (!(terms & SBSE_DIRECT_PARTIAL))
@@ -936,6 +942,32 @@ void ctx_set_error(sbse_ctx *ctx, const std::string &m) { ctx->err = m; }
 
 
 // =============================================================================================
+// D columns (n_c^2 rows, a-major: ab = a n_c + b) of the given canonical slots into out (device,
+// n_c^2 x n_slots row-major)
+template <typename T> int run_direct_block(sbse_ctx *ctx, const std::vector<int> &slots, double *out) {
+  const long long ng = ctx->ng;
+  const int n_c = ctx->n_c, Mab = n_c * n_c, ns = (int)slots.size();
+  cudaStream_t st = ctx->stream;
+  void *vp;
+  int rc;
+  std::vector<int2> xi(Mab);
+  for (int m = 0; m < Mab; ++m) xi[m] = make_int2(ctx->n_occ + m / n_c, ctx->n_occ + m % n_c);
+  if ((rc = ensure(ctx, WS_IDX, (size_t)Mab * sizeof(int2), &vp))) return rc;
+  int2 *xi_dev = (int2 *)vp;
+  CK(cudaMemcpyAsync(xi_dev, xi.data(), Mab * sizeof(int2), cudaMemcpyHostToDevice, st));
+  if ((rc = ensure(ctx, WS_U, (size_t)ns * ng * sizeof(T), &vp))) return rc;
+  T *Wt = (T *)vp;
+  for (int k = 0; k < ns; ++k) {
+    if (sizeof(T) == sizeof(double))
+      CK(cudaMemcpyAsync(Wt + (long long)k * ng, ctx->W + (long long)slots[k] * ng, ng * sizeof(double),
+                         cudaMemcpyDeviceToDevice, st));
+    else
+      launch_convert<T>(ctx->W + (long long)slots[k] * ng, Wt + (long long)k * ng, ng, st);
+  }
+  CHECK_LAUNCH("direct block operands");
+  return contract<T>(ctx, xi_dev, Mab, Wt, ns, out);
+}
+
 extern "C" {
 
 int sbse_create(sbse_ctx **out, int device, int precision) {
@@ -1147,6 +1179,7 @@ int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int
     if (scan_nonfinite(ctx->W + (long long)slots[k] * ctx->ng, ctx->ng, ctx->flag, ctx->stream))
       return fail(ctx, SBSE_ERR_NUMERIC, "W has NaN or Inf (unstable propagation: reduce dt)");
     ctx->have[slots[k]] = 1;
+    ctx->dab_given = false;
   }
   if (w_out)
     for (int k = 0; k < n_pairs; ++k)
@@ -1191,9 +1224,55 @@ int sbse_set_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, const d
     CK(cudaMemcpyAsync(ctx->W + (long long)slots[k] * ctx->ng, w + (long long)k * ctx->ng,
                        ctx->ng * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     ctx->have[slots[k]] = 1;
+    ctx->dab_given = false;
   }
   ctx->have_A = false;
   CK(cudaStreamSynchronize(ctx->stream));
+  return SBSE_OK;
+}
+
+int sbse_get_direct(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, double *dab) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (!pi || !pj || !dab || n_pairs < 1) return fail(ctx, SBSE_ERR_INVALID_ARG, "pairs or dab missing");
+  std::vector<int> slots(n_pairs);
+  for (int k = 0; k < n_pairs; ++k) {
+    if (pi[k] < 0 || pj[k] < pi[k] || pj[k] >= ctx->n_o)
+      return fail(ctx, SBSE_ERR_INVALID_ARG, "pair indices must satisfy 0 <= i <= j < n_o");
+    slots[k] = pair_index(ctx->n_o, pi[k], pj[k]);
+    if (!ctx->have[slots[k]]) return fail(ctx, SBSE_ERR_NOT_READY, "W of a requested pair is not available");
+  }
+  CK(cudaSetDevice(ctx->device));
+  const size_t bytes = (size_t)ctx->n_c * ctx->n_c * n_pairs * sizeof(double);
+  void *vp;
+  int rc;
+  if ((rc = ensure(ctx, WS_DBLK, bytes, &vp))) return rc;
+  rc = ctx->precision == SBSE_FP64 ? run_direct_block<double>(ctx, slots, (double *)vp)
+                                   : run_direct_block<float>(ctx, slots, (double *)vp);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(dab, vp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBSE_OK;
+}
+
+int sbse_set_direct(sbse_ctx *ctx, const double *dab) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (!dab) return fail(ctx, SBSE_ERR_INVALID_ARG, "dab missing");
+  const int P = ctx->n_o * (ctx->n_o + 1) / 2;
+  const size_t cnt = (size_t)ctx->n_c * ctx->n_c * P;
+  for (size_t i = 0; i < cnt; ++i)
+    if (!isfinite(dab[i])) return fail(ctx, SBSE_ERR_NUMERIC, "dab has NaN or Inf");
+  CK(cudaSetDevice(ctx->device));
+  void *vp;
+  int rc;
+  if ((rc = ensure(ctx, WS_DAB, cnt * sizeof(double), &vp))) return rc;
+  CK(cudaMemcpyAsync(vp, dab, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->dab_given = true;
+  ctx->have_A = false;
   return SBSE_OK;
 }
 
@@ -1410,6 +1489,7 @@ int sbse_localize_occupied(sbse_ctx *ctx, int max_sweeps, double tol, double *U_
   launch_convert<float>(ctx->phi64 + (long long)base * ng, ctx->phi32 + (long long)base * ng, (long long)n * ng, st);
   CHECK_LAUNCH("rotate window");
   std::fill(ctx->have.begin(), ctx->have.end(), 0);
+  ctx->dab_given = false;
   ctx->have_A = false;
   ctx->localized = true;
   if (U_out) std::copy(U.begin(), U.end(), U_out);

@@ -1,6 +1,6 @@
 """Finite-box correction W(k -> 0) (Sec. III) through the C ABI against the oracle (GPU only): the
 box-size sweep of one molecule (3 wells drawn for an 8 bohr box, centred in boxes of 8, 10, 12 and
-14 bohr at h = 0.5), deterministic TDH (L = N_occ with the coefficients passed in), FP64: each
+15 bohr at h = 0.5), deterministic TDH (L = N_occ with the coefficients passed in), FP64: each
 run's excitons and boundary potential against oracle/finite_box.py at 1e-10, the fitted eps_eff^-1
 against the oracle's fit, and the corrected spectra overlapping three times better than the raw
 ones; the corrected scissor (sbse_set_scissor) lowers a run's excitons by exactly W(k -> 0)."""
@@ -25,7 +25,7 @@ def test_box_sweep_matches_oracle_and_overlaps(B):
     from paper_2205_06690_gb300 import finite_box as gfb
     base = si.model_system.Preset("fb", N=16, box=8.0, n_wells=3, seed=7, n_occ=2, n_o=2, n_c=3,
                                   n_steps=150, gamma=0.2)
-    systems = [si.make_system(p) for p in si.box_sweep_presets(base, [8.0, 10.0, 12.0, 14.0])]
+    systems = [si.make_system(p) for p in si.box_sweep_presets(base, [8.0, 10.0, 12.0, 15.0])]
     coeff = np.sqrt(2.0) * np.eye(2)
     prm = B.TDHParams(n_s=2, n_steps=150, clean_every=10, dt=0.05, gamma=0.2, alpha=1e-4)
     E, v, s_fit = gfb.box_sweep(systems, prm, 4, precision=B.SBSE_FP64, coeff=coeff)

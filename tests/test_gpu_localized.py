@@ -3,8 +3,8 @@ orbitals) through the C ABI against oracle/localized.py (GPU only). A double wel
 4 bohr apart, 12^3 grid, every eigenpair of the dense H0), N_occ = n_o = 3, n_c = 3, deterministic
 TDH (L = N_occ, coefficients passed in), FP64:
 * sbse_localize_occupied's rotation and sbse_pair_weights equal the oracle's (1e-10);
-* with every pair kept, the excitons in the localized window equal the canonical ones (the
-  rotation is exact; the kick's O(alpha) nonlinearity is below 1e-9 at alpha = 1e-8);
+* with every pair kept and no cleaning, the excitons in the localized window equal the canonical
+  ones (the rotation is exact; the kick's O(alpha) nonlinearity is below 1e-9 at alpha = 1e-8);
 * with the pairs below a pair-density norm threshold screened out (no sbse_apply_W for them,
   SBSE_DIRECT_PARTIAL), the excitons equal the oracle's screened result (1e-10)."""
 import numpy as np
@@ -46,8 +46,9 @@ def test_localized_window_matches_oracle(B):
         c.set_orbitals(n_occ, n_o, n_c, phi, e, 0.5)
         return c
 
+    prm0 = B.TDHParams(n_s=3, n_steps=80, clean_every=0, dt=0.05, gamma=0.2, alpha=1e-8)
     with ctx() as c:
-        c.apply_W(prm, pairs, coeff=coeff)
+        c.apply_W(prm0, pairs, coeff=coeff)
         c.build_A()
         ev_canon = c.spectrum(6)
     U_ref, _ = lo.localize(lo.spread_matrices(g, phi[:n_occ]))
@@ -59,7 +60,7 @@ def test_localized_window_matches_oracle(B):
         assert np.max(np.abs(U - U_ref)) < 1e-10
         w = B.sbse_pair_weights(c.h, n_o)
         assert np.max(np.abs(w - np.array([w_ref[i, j] for i, j in pairs]))) < 1e-10
-        c.apply_W(prm, pairs, coeff=coeff)
+        c.apply_W(prm0, pairs, coeff=coeff)
         c.build_A()
         ev_loc = c.spectrum(6)
         assert np.max(np.abs(ev_loc - ev_canon)) < 1e-9

@@ -304,9 +304,11 @@ def test_graph_replay_matches_direct_launches(B, prec):
 
 def test_pair_shards_reassemble_the_single_run(B, tiny16):
     """The multi-GPU split of a system (paper_2205_06690_gb300.shard): blocks of pairs propagated by
-    separate contexts (here two 'ranks' run in turn on one GPU, gathered on the host) and stored
-    with sbse_set_W give the W, A and excitons of one run over all pairs. FP64; the packing of two
-    pair densities per Poisson transform differs between the runs, hence 1e-12 and not bitwise."""
+    separate contexts (here two 'ranks' run in turn on one GPU), each contracting its own
+    direct-element columns (sbse_get_direct); the gathered columns given to a context that holds no
+    W at all (sbse_set_direct) give the A and excitons of one run over all pairs. FP64; the packing
+    of two pair densities per Poisson transform differs between the runs, hence 1e-12, not bitwise.
+    The W blocks themselves also reassemble (sbse_set_W)."""
     from paper_2205_06690_gb300 import shard
     s = tiny16
     p = s.preset
@@ -323,15 +325,23 @@ def test_pair_shards_reassemble_the_single_run(B, tiny16):
         W_ref = c.apply_W(prm, pairs, copy_out=True)
         A_ref = c.build_A()
         ev_ref = c.spectrum(p.n_exc)
-    blocks = []
+        D_ref = B.sbse_get_direct(c.h, pairs, p.n_c)
+    blocks, cols = [], []
     for r in range(2):
         mine = [pairs[i] for i in shard.pair_block(len(pairs), r, 2)]
         with ctx() as c:
             blocks.append(c.apply_W(prm, mine, copy_out=True))
+            cols.append(B.sbse_get_direct(c.h, mine, p.n_c))
     W = np.concatenate(blocks)
     assert rel_err(W, W_ref) < 1e-12
+    D = np.concatenate(cols, axis=1)
+    assert rel_err(D, D_ref) < 1e-12
     with ctx() as c:
-        B.sbse_set_W(c.h, pairs, W)
+        B.sbse_set_direct(c.h, D)
         A = c.build_A()
         ev = c.spectrum(p.n_exc)
     assert rel_err(A, A_ref) < 1e-12 and rel_err(ev, ev_ref) < 1e-12
+    with ctx() as c:
+        B.sbse_set_W(c.h, pairs, W)
+        A = c.build_A()
+    assert rel_err(A, A_ref) < 1e-12

@@ -47,14 +47,14 @@ def test_fit_recovers_a_known_inverse_dielectric_constant():
 
 
 def test_correction_makes_the_box_sweep_spectra_overlap():
-    """The method on one molecule (3 wells, drawn for an 8 bohr box) in boxes of 8, 10, 12 and 14
+    """The method on one molecule (3 wells, drawn for an 8 bohr box) in boxes of 8, 10, 12 and 15
     bohr at h = 0.5, deterministic TDH (L = N_occ, no stochastic noise), 150 steps: the lowest
     excitons drift with the box size; lowering them by eps_eff^-1 v_bndry with the fitted
     eps_eff^-1 shrinks the spread across boxes at least threefold, with 0 < eps_eff^-1 < 1."""
     base = si.model_system.Preset("fb", N=16, box=8.0, n_wells=3, seed=7, n_occ=2, n_o=2, n_c=3,
                                   n_steps=150, gamma=0.2)
     E, v = [], []
-    for p in si.box_sweep_presets(base, [8.0, 10.0, 12.0, 14.0]):
+    for p in si.box_sweep_presets(base, [8.0, 10.0, 12.0, 15.0]):
         s = si.make_system(p)
         g = tdh.Grid(p.N, p.box)
         coeff = np.sqrt(p.n_occ) * np.eye(p.n_occ)

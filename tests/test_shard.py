@@ -1,6 +1,7 @@
-"""Pair sharding across ranks (paper_2205_06690_gb300.shard): partition and the all-gather of W,
-tested with two gloo ranks on the CPU. The W of each block come from the FP64 oracle, so the
-gathered set and the A assembled from it must equal the single-process result exactly."""
+"""Pair sharding across ranks (paper_2205_06690_gb300.shard): partition, the all-gather of W and the
+all-gather of the direct-element columns (the exchange of the sharded path: n_c^2 numbers per
+pair), tested with gloo ranks on the CPU. The W of each block come from the FP64 oracle, so the
+gathered sets and the A assembled from them must equal the single-process result exactly."""
 import os
 import socket
 
@@ -54,6 +55,12 @@ def _worker(rank, world, port, out_dir):
         w_local = np.array([w[p].reshape(-1) for p in mine]).reshape(len(mine), -1)
         w_all = shard.gather_W(w_local, len(pairs), rank, world)
         np.save(os.path.join(out_dir, f"w{rank}.npy"), w_all)
+        # this rank's direct-element columns D[ab][pair] = dV sum_r phi_a phi_b W_ij, then their gather
+        _, _, phi_c, _ = tdh.windows(phi, eps, n_occ, n_o, n_c)
+        C = phi_c.reshape(n_c, -1)
+        cols = np.array([((C[:, None, :] * C[None, :, :]).reshape(n_c * n_c, -1) @ w[p].reshape(-1)) * g.dV
+                         for p in mine]).T.reshape(n_c * n_c, len(mine))
+        np.save(os.path.join(out_dir, f"d{rank}.npy"), shard.gather_columns(cols, len(pairs), rank, world))
     finally:
         dist.destroy_process_group()
 
@@ -68,9 +75,21 @@ def test_gathered_W_and_A_equal_the_single_process_result(tmp_path, world):
     ref_arr = np.array([ref[p].reshape(-1) for p in pairs])
     phi_o, eps_o, phi_c, eps_c = tdh.windows(phi, eps, n_occ, n_o, n_c)
     A_ref = tdh.assemble_A(eps_o, eps_c, 0.5, tdh.exchange_K(g, phi_o, phi_c), tdh.direct_D(g, phi_o, phi_c, ref))
+    C = phi_c.reshape(n_c, -1)
+    d_ref = np.array([((C[:, None, :] * C[None, :, :]).reshape(n_c * n_c, -1) @ ref[p].reshape(-1)) * g.dV
+                      for p in pairs]).T
     for r in range(world):
         w_all = np.load(tmp_path / f"w{r}.npy")
         assert np.array_equal(w_all, ref_arr)
+        d_all = np.load(tmp_path / f"d{r}.npy")
+        assert np.array_equal(d_all, d_ref)
+        # D[ia, jb] from the gathered columns equals the oracle's direct element
+        Dm = np.zeros((n_o * n_c, n_o * n_c))
+        for k, (i, j) in enumerate(pairs):
+            blk = d_all[:, k].reshape(n_c, n_c)
+            Dm[i * n_c:(i + 1) * n_c, j * n_c:(j + 1) * n_c] = blk
+            Dm[j * n_c:(j + 1) * n_c, i * n_c:(i + 1) * n_c] = blk.T
+        assert np.allclose(Dm, tdh.direct_D(g, phi_o, phi_c, ref), rtol=0, atol=1e-14)
         w_dict = {p: w_all[k].reshape(phi.shape[1:]) for k, p in enumerate(pairs)}
         A = tdh.assemble_A(eps_o, eps_c, 0.5, tdh.exchange_K(g, phi_o, phi_c), tdh.direct_D(g, phi_o, phi_c, w_dict))
         assert np.array_equal(A, A_ref)
