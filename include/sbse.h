@@ -222,6 +222,32 @@ int sbse_fit_inverse_dielectric(int n_box, int k, const double *E, const double 
 int sbse_localize_occupied(sbse_ctx *ctx, int max_sweeps, double tol, double *U_out);
 int sbse_pair_weights(sbse_ctx *ctx, double *w_out);
 
+/* Mixed hole-grid representation (Sec. II.C, "Mixed Representation Iterative Solution"): the BSE
+ * operator A = Q A-bar on vectors f_j(r), one grid function per window state j (n_o x n^3, x
+ * fastest, FP64), (A-bar f)_j = (H0 + Delta - eps_j) f_j + dv phi_j - sum_i f_i W_ij with
+ * dv = v dn, dn = 2 sum_i phi_i f_i (the window's exciton density), W_ji = W_ij from sbse_apply_W.
+ * projector: 0 = SBSE_Q_OCCUPIED, Q = 1 - sum_{s <= N_occ} |phi_s><phi_s| (the whole virtual space
+ * of the grid); 1 = SBSE_Q_CONDUCTION, Q = sum_{c <= n_c} |phi_c><phi_c| (the electron-hole-basis
+ * variant; A restricted to span{phi_c} is then the matrix of Eq. 1). All FP64 on the device in
+ * either precision mode. Require W for every window pair and the canonical (not localized) window.
+ * sbse_apply_A_mixed: f_out = A f_in (host arrays, n_o x n^3 each).
+ * sbse_mixed_bounds: an interval [lo, hi] enclosing the spectrum of A on the range of Q: the
+ *   extreme Ritz values of n_lanczos Lanczos steps from f0_j = Q x phi_j (x along `axis` from the box
+ *   centre; each vector projected by Q), widened by 5 % of their spread on each side.
+ * sbse_absorption_mixed: sigma(omega) = omega <f0| delta(A - omega) |f0> with f0_j = Q x phi_j, from
+ *   n_terms residues R_n = <f0| T_n(A~) |f0>, A~ f = Q(A-bar f - c f) / w, c = (lo + hi) / 2,
+ *   w = (hi - lo) / 2 for the interval [lo, hi] the caller gives (it must enclose the spectrum), and
+ *   the Gaussian-smoothed delta of sbse_absorption (Chebyshev-Gauss quadrature on n_terms nodes).
+ *   sigma: host n_omega; residues: optional host n_terms.
+ * Errors: INVALID_ARG, NOT_READY (orbitals or some W missing), UNSUPPORTED (localized window), OOM,
+ * NUMERIC, CUDA. */
+#define SBSE_Q_OCCUPIED 0
+#define SBSE_Q_CONDUCTION 1
+int sbse_apply_A_mixed(sbse_ctx *ctx, int projector, const double *f_in, double *f_out);
+int sbse_mixed_bounds(sbse_ctx *ctx, int projector, int axis, int n_lanczos, double *lo, double *hi);
+int sbse_absorption_mixed(sbse_ctx *ctx, int projector, int axis, int n_terms, double lo, double hi,
+                          double broadening, int n_omega, const double *omega, double *sigma, double *residues);
+
 /* Replace the scissor shift Delta of Eq. (9) (e.g. by Delta - eps_eff^-1 v_bndry) without touching
  * orbitals or W; A must be built again. Errors: INVALID_ARG, NOT_READY, NUMERIC. */
 int sbse_set_scissor(sbse_ctx *ctx, double scissor);

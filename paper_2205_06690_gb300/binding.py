@@ -33,6 +33,8 @@ SBSE_COEFF_SIGN = 1
 SBSE_EXCHANGE = 1
 SBSE_DIRECT = 2
 SBSE_DIRECT_PARTIAL = 4
+SBSE_Q_OCCUPIED = 0
+SBSE_Q_CONDUCTION = 1
 SBSE_OPT_TENSOR_CORES = 1
 SBSE_OPT_CHUNK_MB = 2
 SBSE_OPT_PERSISTENT = 3
@@ -111,6 +113,9 @@ def load() -> C.CDLL:
         "sbse_pair_weights": (i, [vp, dp]),
         "sbse_get_direct": (i, [vp, i, ip, ip, dp]),
         "sbse_set_direct": (i, [vp, dp]),
+        "sbse_apply_A_mixed": (i, [vp, i, dp, dp]),
+        "sbse_mixed_bounds": (i, [vp, i, i, i, dp, dp]),
+        "sbse_absorption_mixed": (i, [vp, i, i, i, d, d, d, i, dp, dp, dp]),
     }
     fp = C.POINTER(C.c_float)
     sig.update({
@@ -332,6 +337,30 @@ def sbse_get_direct(ctx, pairs, n_c: int):
 
 def sbse_set_direct(ctx, dab) -> None:
     _check(ctx, load().sbse_set_direct(ctx, _dptr(_f64(dab))))
+
+
+def sbse_apply_A_mixed(ctx, projector: int, f):
+    """A f in the mixed hole-grid representation (f: n_o x n^3 host array)."""
+    fa = _f64(f)
+    out = np.empty_like(fa)
+    _check(ctx, load().sbse_apply_A_mixed(ctx, projector, _dptr(fa), _dptr(out)))
+    return out
+
+
+def sbse_mixed_bounds(ctx, projector: int, axis: int, n_lanczos: int):
+    lo, hi = C.c_double(), C.c_double()
+    _check(ctx, load().sbse_mixed_bounds(ctx, projector, axis, n_lanczos, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def sbse_absorption_mixed(ctx, projector: int, axis: int, n_terms: int, lo: float, hi: float, broadening: float,
+                          omega):
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1))
+    sig = np.empty_like(om)
+    res = np.empty(n_terms)
+    _check(ctx, load().sbse_absorption_mixed(ctx, projector, axis, n_terms, float(lo), float(hi), float(broadening),
+                                             len(om), _dptr(om), _dptr(sig), _dptr(res)))
+    return sig, res
 
 
 def sbse_set_scissor(ctx, scissor: float) -> None:

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsbse.so")
-SOURCES = ["sbse_api.cu", "tdh_kernels.cu", "fft_fast.cu", "fft_split.cu", "contract.cu", "eig.cu", "noalloc.cu", "umma_gemm.cu", "fno.cu", "spectrum.cu", "finite_box.cu", "localized.cu"]
+SOURCES = ["sbse_api.cu", "tdh_kernels.cu", "fft_fast.cu", "fft_split.cu", "contract.cu", "eig.cu", "noalloc.cu", "umma_gemm.cu", "fno.cu", "spectrum.cu", "finite_box.cu", "localized.cu", "mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -205,6 +205,10 @@ __device__ __forceinline__ void zcol_column(const GView<T> &g, C2<T> *data, long
     const C mxy = cscale(cmul(g.kin[x], g.kin[y]), inv_ng);
 #pragma unroll
     for (int z = 0; z < N; ++z) v[z] = cmul(v[z], cmul(mxy, g.kin[z]));
+  } else if (mult == Z_HALF_G2) {
+    const T gxy = g.k2[x] + g.k2[y];
+#pragma unroll
+    for (int z = 0; z < N; ++z) v[z] = cscale(v[z], T(0.5) * (gxy + g.k2[z]) * inv_ng);
   } else {
     const T gxy = g.k2[x] + g.k2[y];
 #pragma unroll

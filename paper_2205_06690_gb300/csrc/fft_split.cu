@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(128, 4) k_zcol2(GView<float> g, float2 *data, 
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const float G2 = gxy + g.k2[h * H + s * Q + j];
-        v[h * Q + j] = cscale(v[h * Q + j], G2 > 0.f ? float(4.0 * M_PI) * inv_ng / G2 : 0.f);
+        const float f = mult == Z_HALF_G2 ? 0.5f * G2 * inv_ng : (G2 > 0.f ? float(4.0 * M_PI) * inv_ng / G2 : 0.f);
+        v[h * Q + j] = cscale(v[h * Q + j], f);
       }
     }
   }

@@ -94,7 +94,9 @@ template <typename T> void launch_phase_table(const double *v64, long long ng, d
                                               cudaStream_t s);
 template <typename T> void launch_ypass(const GridTables<T> &g, C2<T> *data, int n_items, int sign,
                                         cudaStream_t s);
-enum ZMult { Z_KINETIC = 0, Z_POISSON = 1 };
+// multiplier of the z pass: kinetic propagator, Coulomb kernel 4 pi / |G|^2 (G = 0 dropped), or the
+// kinetic energy |G|^2 / 2 (the spectral -1/2 Laplacian); each with the 1/N^3 of the round trip
+enum ZMult { Z_KINETIC = 0, Z_POISSON = 1, Z_HALF_G2 = 2 };
 template <typename T> void launch_zpass(const GridTables<T> &g, C2<T> *data, int n_items, int mult,
                                         cudaStream_t s);
 // inverse x pass of orbitals; with dens != nullptr, items are grouped L per pair and the induced
@@ -209,6 +211,27 @@ void launch_rotate_rows(const double *phi, int base, int n, const double *U, lon
 size_t pair_norms_work_doubles(int n_pairs);
 void launch_pair_norms(const double *phi, const int2 *pairs, int n_pairs, long long ng, double scale,
                        double *work, double *out, cudaStream_t s);
+
+// ---- mixed hole-grid representation of A (mixed.cu), FP64; f, out: n_o rows of ng points
+void launch_exciton_density(const double *phi_o, const double *f, int n_o, long long ng, double *dn, cudaStream_t s);
+// out_j = tf_j + (v + scissor - eps_j - shift) f_j + dv phi_j - sum_i f_i W_ij
+void launch_abar(const double *tf, const double *f, const double *v, const double *eps_o, double scissor, double shift,
+                 const double *dv, const double *phi_o, const double *W, int n_o, long long ng, double *out,
+                 cudaStream_t s);
+// keep = 0: out_j -= sum_s <basis_s|out_j> basis_s; keep = 1: out_j = sum_s <basis_s|out_j> basis_s
+size_t project_work_doubles(int n_o, int n_b, long long ng);
+void launch_project(double *out, int n_o, const double *basis, int n_b, long long ng, double dV, int keep,
+                    double *work, cudaStream_t s);
+void launch_coord_times(const double *phi_o, int n_o, int N, double h, double box, int axis, double *out,
+                        cudaStream_t s);
+void launch_axpby(double a, const double *x, double b, double *y, long long n, cudaStream_t s);
+size_t dot_work_doubles();
+// out[0] = scale x . y (fixed-order reduction)
+void launch_dot(const double *x, const double *y, long long n, double scale, double *work, double *out,
+                cudaStream_t s);
+// sigma(omega) from residues R (K of them) with cw = {c, w}: D (K doubles) scratch (spectrum.cu)
+void launch_sigma_from_residues(const double *R, int K, const double *cw, const double *omega, int n_omega,
+                                double s, double *D, double *sigma, cudaStream_t st);
 
 // ---- absorption spectrum by a Chebyshev expansion of A (spectrum.cu)
 struct SpectrumBufs {

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <atomic>
 #include <new>
+#include <mutex>
+#include <shared_mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -104,7 +106,7 @@ namespace {
 
 enum Ws {
   WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX, WS_LOC, WS_DBLK
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX, WS_LOC, WS_DBLK, WS_MIX
 };
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
@@ -129,6 +131,11 @@ int cuda_fail(sbse_ctx *c, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);  \
   } while (0)
 
+// Graph captures of different contexts may run in parallel host threads; cudaMalloc / cudaFree
+// from one thread while another thread's stream is being captured invalidates that capture. So
+// captures hold this lock shared and allocations hold it exclusively.
+std::shared_mutex g_capture_mx;
+
 // Every device allocation of a context goes through dalloc / release, which keep the context's
 // total (SBSE_OPT_MEM_LIMIT_MB refuses an allocation that would exceed the limit).
 template <typename X> int dalloc(sbse_ctx *ctx, X **p, size_t bytes) {
@@ -138,7 +145,11 @@ template <typename X> int dalloc(sbse_ctx *ctx, X **p, size_t bytes) {
     return fail(ctx, SBSE_ERR_OOM, "device allocation of " + std::to_string(bytes) +
                                        " bytes would exceed the context's memory limit of " +
                                        std::to_string(ctx->mem_limit) + " bytes");
-  cudaError_t e = cudaMalloc((void **)p, bytes);
+  cudaError_t e;
+  {
+    std::unique_lock<std::shared_mutex> lk(g_capture_mx);
+    e = cudaMalloc((void **)p, bytes);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -156,6 +167,7 @@ void release(sbse_ctx *ctx, void *p) {
     ctx->held_bytes -= it->second;
     ctx->held.erase(it);
   }
+  std::unique_lock<std::shared_mutex> lk(g_capture_mx);
   cudaFree(p);
 }
 
@@ -411,18 +423,18 @@ void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T
 // Poisson round trip of packed slots (fa.mode is XF_PACK_DN or XF_PACK_PROD)
 template <typename T>
 void round_trip_poisson(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T> &fa,
-                        const PoissonOut &po, T *u_out, T *acc, C2<T> *em1_out) {
+                        const PoissonOut &po, T *u_out, T *acc, C2<T> *em1_out, int zmult = Z_POISSON) {
   cudaStream_t st = ctx->stream;
   C2<T> *pw = fa.out;
   const int S = fa.n_items;
   if (fast_supported<T>(g.N)) {
     launch_plane_fwd<T>(g, fa, st);
-    launch_zcol<T>(g, pw, S, Z_POISSON, st);  // few items: the plain column kernel has more blocks
+    launch_zcol<T>(g, pw, S, zmult, st);  // few items: the plain column kernel has more blocks
     launch_plane_inv_poisson<T>(g, pw, S, po, u_out, acc, em1_out, st);
   } else {
     launch_xfwd<T>(g, fa, st);
     launch_ypass<T>(g, pw, S, -1, st);
-    launch_zpass<T>(g, pw, S, Z_POISSON, st);
+    launch_zpass<T>(g, pw, S, zmult, st);
     launch_ypass<T>(g, pw, S, +1, st);
     launch_xinv_poisson<T>(g, pw, S, po, u_out, acc, em1_out, st);
   }
@@ -755,6 +767,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
         ctx->graph_exec = nullptr;
       }
       cudaGraph_t graph = nullptr;
+      std::shared_lock<std::shared_mutex> capture_lock(g_capture_mx);
       if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
         // launches issued while capturing are counted once here; they run in the replay below
         const long long l0 = g_launches.load();
@@ -966,6 +979,113 @@ template <typename T> int run_direct_block(sbse_ctx *ctx, const std::vector<int>
   }
   CHECK_LAUNCH("direct block operands");
   return contract<T>(ctx, xi_dev, Mab, Wt, ns, out);
+}
+
+// ---- mixed hole-grid representation (Sec. II.C): A = Q A-bar on f_j(r), FP64 on the device
+struct MixedBufs {
+  double *tf, *dn, *dv, *pwork, *dwork;
+  C2<double> *pw;
+};
+
+int mixed_bufs(sbse_ctx *ctx, int n_extra_fields, MixedBufs *mb, double **extra) {
+  const long long ng = ctx->ng;
+  const int n_o = ctx->n_o;
+  const int nb = std::max(ctx->n_occ, ctx->n_c);
+  const size_t pwd = project_work_doubles(n_o, nb, ng);
+  const size_t doubles = (size_t)n_o * ng + 2 * (size_t)ng + pwd + dot_work_doubles() + (size_t)n_extra_fields * n_o * ng;
+  void *vp;
+  int rc;
+  if ((rc = ensure(ctx, WS_MIX, doubles * sizeof(double), &vp))) return rc;
+  double *p = (double *)vp;
+  mb->tf = p;
+  mb->dn = mb->tf + (long long)n_o * ng;
+  mb->dv = mb->dn + ng;
+  mb->pwork = mb->dv + ng;
+  mb->dwork = mb->pwork + pwd;
+  *extra = mb->dwork + dot_work_doubles();
+  if ((rc = ensure(ctx, WS_PW, (size_t)((n_o + 1) / 2) * ng * sizeof(C2<double>), &vp))) return rc;
+  mb->pw = (C2<double> *)vp;
+  return SBSE_OK;
+}
+
+// out = Q (A-bar - shift) f for the n_o window rows f (device); projector 0: Q = 1 - P_occ, 1: onto
+// the conduction states
+int mixed_apply(sbse_ctx *ctx, int projector, const double *f, double *out, double shift, const MixedBufs &mb) {
+  const long long ng = ctx->ng;
+  const int n_o = ctx->n_o;
+  const double *phi_o = ctx->phi64 + (long long)(ctx->n_occ - n_o) * ng;
+  cudaStream_t st = ctx->stream;
+  XfwdArgs<double> xa{};
+  xa.mode = XF_PACK_DN;
+  xa.n_items = (n_o + 1) / 2;
+  xa.out = mb.pw;
+  xa.dn = f;
+  xa.n_dn = n_o;
+  round_trip_poisson<double>(ctx, ctx->g64, xa, PoissonOut{n_o, 1.0, 0.0, 0.0}, mb.tf, nullptr, nullptr, Z_HALF_G2);
+  launch_exciton_density(phi_o, f, n_o, ng, mb.dn, st);
+  int rc;
+  if ((rc = poisson<double>(ctx, ctx->g64, mb.dn, 1, mb.pw, mb.dv, nullptr, 0.0, nullptr, 0.0))) return rc;
+  launch_abar(mb.tf, f, ctx->v64, ctx->eps_dev, ctx->scissor, shift, mb.dv, phi_o, ctx->W, n_o, ng, out, st);
+  if (projector == 0)
+    launch_project(out, n_o, ctx->phi64, ctx->n_occ, ng, ctx->dV, 0, mb.pwork, st);
+  else
+    launch_project(out, n_o, ctx->phi64 + (long long)ctx->n_occ * ng, ctx->n_c, ng, ctx->dV, 1, mb.pwork, st);
+  CHECK_LAUNCH("mixed A");
+  return SBSE_OK;
+}
+
+int mixed_ready(sbse_ctx *ctx, int projector) {
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (projector != 0 && projector != 1) return fail(ctx, SBSE_ERR_INVALID_ARG, "projector must be 0 or 1");
+  if (ctx->localized) return fail(ctx, SBSE_ERR_UNSUPPORTED, "the mixed representation needs the canonical window");
+  for (char h : ctx->have)
+    if (!h) return fail(ctx, SBSE_ERR_NOT_READY, "W missing for some pairs: call sbse_apply_W for all pairs first");
+  return SBSE_OK;
+}
+
+// f0_j = Q x phi_j (device)
+void mixed_start(sbse_ctx *ctx, int projector, int axis, double *f0, const MixedBufs &mb) {
+  const long long ng = ctx->ng;
+  const int n_o = ctx->n_o;
+  launch_coord_times(ctx->phi64 + (long long)(ctx->n_occ - n_o) * ng, n_o, ctx->N, ctx->h, ctx->box, axis, f0,
+                     ctx->stream);
+  if (projector == 0)
+    launch_project(f0, n_o, ctx->phi64, ctx->n_occ, ng, ctx->dV, 0, mb.pwork, ctx->stream);
+  else
+    launch_project(f0, n_o, ctx->phi64 + (long long)ctx->n_occ * ng, ctx->n_c, ng, ctx->dV, 1, mb.pwork, ctx->stream);
+}
+
+// smallest and largest eigenvalue of the symmetric tridiagonal matrix (al, be) by Sturm bisection
+void tridiag_extremes(const std::vector<double> &al, const std::vector<double> &be, double *lo, double *hi) {
+  const int m = (int)al.size();
+  double glo = INFINITY, ghi = -INFINITY;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+    glo = std::min(glo, al[i] - r);
+    ghi = std::max(ghi, al[i] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int c = 0;
+    double d = al[0] - x;
+    if (d < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      if (d == 0.0) d = 1e-300;
+      d = al[i] - x - be[i - 1] * be[i - 1] / d;
+      if (d < 0) ++c;
+    }
+    return c;
+  };
+  auto kth = [&](int k) {  // k-th smallest eigenvalue (0-based)
+    double a = glo, b = ghi;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (count_below(mid) > k) b = mid;
+      else a = mid;
+    }
+    return 0.5 * (a + b);
+  };
+  *lo = kth(0);
+  *hi = kth(m - 1);
 }
 
 extern "C" {
@@ -1520,6 +1640,131 @@ int sbse_pair_weights(sbse_ctx *ctx, double *w_out) {
   CK(cudaMemcpyAsync(w_out, out, P * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   for (int p = 0; p < P; ++p) w_out[p] = sqrt(w_out[p]);
+  return SBSE_OK;
+}
+
+int sbse_apply_A_mixed(sbse_ctx *ctx, int projector, const double *f_in, double *f_out) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!f_in || !f_out) return fail(ctx, SBSE_ERR_INVALID_ARG, "f_in or f_out missing");
+  int rc;
+  if ((rc = mixed_ready(ctx, projector))) return rc;
+  CK(cudaSetDevice(ctx->device));
+  const size_t bytes = (size_t)ctx->n_o * ctx->ng * sizeof(double);
+  MixedBufs mb;
+  double *ex;
+  if ((rc = mixed_bufs(ctx, 2, &mb, &ex))) return rc;
+  double *f = ex, *out = ex + (long long)ctx->n_o * ctx->ng;
+  CK(cudaMemcpyAsync(f, f_in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  if ((rc = mixed_apply(ctx, projector, f, out, 0.0, mb))) return rc;
+  CK(cudaMemcpyAsync(f_out, out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBSE_OK;
+}
+
+int sbse_mixed_bounds(sbse_ctx *ctx, int projector, int axis, int n_lanczos, double *lo, double *hi) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!lo || !hi || axis < 0 || axis > 2 || n_lanczos < 2 || n_lanczos > 10000)
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "need lo, hi, axis in 0..2 and 2 <= n_lanczos <= 10000");
+  int rc;
+  if ((rc = mixed_ready(ctx, projector))) return rc;
+  CK(cudaSetDevice(ctx->device));
+  const long long n = (long long)ctx->n_o * ctx->ng;
+  cudaStream_t st = ctx->stream;
+  MixedBufs mb;
+  double *ex;
+  if ((rc = mixed_bufs(ctx, 3, &mb, &ex))) return rc;
+  double *q = ex, *qp = ex + n, *z = ex + 2 * n;
+  double *dev_s = mb.dwork + dot_work_doubles() - 1;  // (the dot scratch's last slot is free: 256 partials use it all)
+  (void)dev_s;
+  void *vp;
+  if ((rc = ensure(ctx, WS_EIG, 8 * sizeof(double), &vp))) return rc;
+  double *sc = (double *)vp;
+  auto dot = [&](const double *x, const double *y) -> double {
+    double h = 0.0;
+    launch_dot(x, y, n, ctx->dV, mb.dwork, sc, st);
+    cudaMemcpyAsync(&h, sc, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return h;
+  };
+  mixed_start(ctx, projector, axis, q, mb);
+  const double n0 = sqrt(dot(q, q));
+  if (!(n0 > 0.0)) return fail(ctx, SBSE_ERR_NUMERIC, "the start vector vanishes");
+  launch_axpby(0.0, q, 1.0 / n0, q, n, st);
+  CK(cudaMemsetAsync(qp, 0, n * sizeof(double), st));
+  std::vector<double> al, be;
+  double b = 0.0;
+  for (int k = 0; k < n_lanczos; ++k) {
+    if ((rc = mixed_apply(ctx, projector, q, z, 0.0, mb))) return rc;
+    launch_axpby(-b, qp, 1.0, z, n, st);
+    const double a = dot(q, z);
+    launch_axpby(-a, q, 1.0, z, n, st);
+    if (projector == 0)
+      launch_project(z, ctx->n_o, ctx->phi64, ctx->n_occ, ctx->ng, ctx->dV, 0, mb.pwork, st);
+    else
+      launch_project(z, ctx->n_o, ctx->phi64 + (long long)ctx->n_occ * ctx->ng, ctx->n_c, ctx->ng, ctx->dV, 1,
+                     mb.pwork, st);
+    al.push_back(a);
+    b = sqrt(dot(z, z));
+    if (k == n_lanczos - 1 || b == 0.0) break;
+    be.push_back(b);
+    std::swap(q, qp);           // qp <- q
+    launch_axpby(1.0 / b, z, 0.0, q, n, st);  // q <- z / b (q now points at the old qp buffer)
+  }
+  CHECK_LAUNCH("lanczos");
+  double tlo, thi;
+  tridiag_extremes(al, be, &tlo, &thi);
+  const double spread = thi - tlo;
+  *lo = tlo - 0.05 * spread;
+  *hi = thi + 0.05 * spread;
+  return SBSE_OK;
+}
+
+int sbse_absorption_mixed(sbse_ctx *ctx, int projector, int axis, int n_terms, double lo, double hi,
+                          double broadening, int n_omega, const double *omega, double *sigma, double *residues) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (axis < 0 || axis > 2 || n_terms < 2 || n_terms > 65536 || !(broadening > 0.0) || n_omega < 1 ||
+      n_omega > (1 << 24) || !omega || !sigma || !(hi > lo))
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "bad axis, n_terms, interval, broadening or frequency arrays");
+  int rc;
+  if ((rc = mixed_ready(ctx, projector))) return rc;
+  CK(cudaSetDevice(ctx->device));
+  const long long n = (long long)ctx->n_o * ctx->ng;
+  cudaStream_t st = ctx->stream;
+  MixedBufs mb;
+  double *ex;
+  if ((rc = mixed_bufs(ctx, 4, &mb, &ex))) return rc;
+  double *f0 = ex, *va = ex + n, *vb = ex + 2 * n, *tmp = ex + 3 * n;
+  void *vp;
+  if ((rc = ensure(ctx, WS_SPEC, (2 * (size_t)n_terms + 2 * (size_t)n_omega + 2) * sizeof(double), &vp))) return rc;
+  double *R = (double *)vp, *D = R + n_terms, *om = D + n_terms, *sg = om + n_omega, *cw = sg + n_omega;
+  const double c = 0.5 * (lo + hi), w = 0.5 * (hi - lo);
+  const double cwh[2] = {c, w};
+  CK(cudaMemcpyAsync(cw, cwh, sizeof(cwh), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(om, omega, (size_t)n_omega * sizeof(double), cudaMemcpyHostToDevice, st));
+  mixed_start(ctx, projector, axis, f0, mb);
+  // v_0 = f0 (in va), v_1 = A~ f0 (in vb), v_{t+1} = 2 A~ v_t - v_{t-1} overwriting v_{t-1}
+  CK(cudaMemcpyAsync(va, f0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_dot(f0, va, n, ctx->dV, mb.dwork, R, st);
+  double *prev = va, *cur = vb;
+  if ((rc = mixed_apply(ctx, projector, va, tmp, c, mb))) return rc;
+  launch_axpby(1.0 / w, tmp, 0.0, cur, n, st);
+  for (int t = 1; t < n_terms; ++t) {
+    launch_dot(f0, cur, n, ctx->dV, mb.dwork, R + t, st);
+    if (t + 1 == n_terms) break;
+    if ((rc = mixed_apply(ctx, projector, cur, tmp, c, mb))) return rc;
+    launch_axpby(2.0 / w, tmp, -1.0, prev, n, st);  // prev <- 2 A~ cur - prev = v_{t+1}
+    std::swap(prev, cur);
+  }
+  launch_sigma_from_residues(R, n_terms, cw, om, n_omega, broadening, D, sg, st);
+  CHECK_LAUNCH("mixed absorption");
+  CK(cudaMemcpyAsync(sigma, sg, (size_t)n_omega * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (residues) CK(cudaMemcpyAsync(residues, R, (size_t)n_terms * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int j = 0; j < n_omega; ++j)
+    if (!isfinite(sigma[j])) return fail(ctx, SBSE_ERR_NUMERIC, "spectrum is not finite (interval too narrow?)");
   return SBSE_OK;
 }
 

@@ -154,6 +154,13 @@ SpectrumBufs spectrum_bufs(double *work, int n, int n_terms, int n_omega) {
   return b;
 }
 
+void launch_sigma_from_residues(const double *R, int K, const double *cw, const double *omega, int n_omega,
+                                double s, double *D, double *sigma, cudaStream_t st) {
+  k_cheb_density<<<(K + 127) / 128, 128, 0, st>>>(R, K, D);
+  k_sigma<<<(n_omega + 127) / 128, 128, 0, st>>>(D, K, cw, omega, n_omega, s, sigma);
+  count_launch(2);
+}
+
 void launch_absorption(const SpectrumBufs &b, const double *phi_o, const double *phi_c, int n_o, int n_c, int N,
                        double h, double box, double dV, const double *A, int axis, int n_terms, double s,
                        int n_omega, cudaStream_t st) {

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_zpass(GView<T> g, C2<T> *data, int
       v = cscale(cmul(v, m), inv_ng);
     } else {
       const T G2 = g.k2[kx] + g.k2[y] + g.k2[e];
-      const T f = G2 > T(0) ? T(4.0 * M_PI) / G2 * inv_ng : T(0);
+      const T f = mult == Z_HALF_G2 ? T(0.5) * G2 * inv_ng : (G2 > T(0) ? T(4.0 * M_PI) / G2 * inv_ng : T(0));
       v = cscale(v, f);
     }
     R[e * ld + p] = v;
