@@ -255,6 +255,7 @@ def batch_bench(args):
     import torch
 
     os.environ.setdefault("SBSE_EIGENSOLVER", "chfsi")  # orbitals of 64 systems: on the GPU
+    os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")  # no module loads during other threads' captures
     import sbse_inputs as si
     from paper_2205_06690_gb300 import batch
     from paper_2205_06690_gb300 import binding as B

@@ -3,7 +3,10 @@
 A `Batch` keeps one context (device memory, CUDA stream, captured graph of the time loop) per
 system; `Batch.run` issues the systems' calls from a pool of host threads (the C calls release the
 interpreter lock), so their kernels run concurrently on the GPU and fill it even when one system
-alone would not, and from the second run on every system's time loop is a graph replay.
+alone would not, and from the second run on every system's time loop is a graph replay. The first
+run of a batch goes one system at a time: under CUDA's lazy module loading the first launch of a
+kernel loads its module, which would invalidate another thread's graph capture in progress; after
+one run every kernel is loaded and every graph captured.
 `autotune` picks, per grid size, the fastest split-operator variant that the grid supports (three
 pass kernels or the persistent step kernel; plain or bulk-copy streamed passes) from a short timed
 trial, and caches the choice.
@@ -72,6 +75,7 @@ class Batch:
     def __init__(self, items, precision: int = B.SBSE_MIXED, device: int = 0):
         self.items = list(items)
         self.precision = precision
+        self.warm = False
         self.ctx = []
         for it in self.items:
             c = B.Context(device, precision)
@@ -95,8 +99,9 @@ class Batch:
         """Whole hot path (all pairs, A, excitons) of every system; per-system results and the
         wall time of the batch."""
         t0 = time.perf_counter()
-        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        with cf.ThreadPoolExecutor(max_workers=workers if self.warm else 1) as ex:
             res = list(ex.map(lambda i: self._one(i, params, tune), range(len(self.items))))
+        self.warm = True
         return res, time.perf_counter() - t0
 
     def close(self):

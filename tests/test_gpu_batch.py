@@ -19,7 +19,9 @@ def test_concurrent_batch_of_uneven_grids_matches_separate_runs():
         s = si.make_system(p)
         items.append(batch.BatchItem(n, p.box, s.v_loc, s.phi, s.eps, n_occ, 3, 4, 0.5, 4))
     prm = B.TDHParams(n_s=10, n_steps=40, clean_every=10, dt=0.05, gamma=0.1, alpha=1e-4, seed=7)
-    res, wall = batch.run_batch(items, prm, precision=B.SBSE_FP64, workers=5, tune=True)
+    with batch.Batch(items, B.SBSE_FP64) as bt:
+        bt.run(prm, workers=5, tune=True)  # the first run goes one system at a time
+        res, wall = bt.run(prm, workers=5, tune=True)  # concurrent graph replays
     for it, r in zip(items, res):
         ref, _ = batch.run_batch([it], prm, precision=B.SBSE_FP64, workers=1, tune=False)
         assert np.array_equal(r["excitons"], ref[0]["excitons"])
