@@ -167,11 +167,11 @@ int launch_eig_lowest(double *A, int n, int k, double *evals_dev, double *work, 
   const size_t sm_full = sm + (size_t)n * n * sizeof(double);
   if (n >= 3) {
     if (sm_full <= 200 * 1024) {
-      cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_full);
+      raise_smem_limit((const void *)k_tridiag<true>, sm_full);
       k_tridiag<true><<<1, kEigThreads, sm_full, s>>>(Aw, n, dg, of, nullptr, nullptr);
     } else {
       if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        raise_smem_limit((const void *)k_tridiag<false>, sm);
       k_tridiag<false><<<1, kEigThreads, sm, s>>>(Aw, n, dg, of, nullptr, nullptr);
     }
     count_launch(1);
@@ -343,11 +343,11 @@ int launch_eig_vectors(const double *A, int n, int k, double *evals_dev, double 
   const size_t sm_full = sm + (size_t)n * n * sizeof(double);
   if (n >= 3) {
     if (sm_full <= 200 * 1024) {
-      cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_full);
+      raise_smem_limit((const void *)k_tridiag<true>, sm_full);
       k_tridiag<true><<<1, kEigThreads, sm_full, s>>>(Aw, n, dg, of, refl, betas);
     } else {
       if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        raise_smem_limit((const void *)k_tridiag<false>, sm);
       k_tridiag<false><<<1, kEigThreads, sm, s>>>(Aw, n, dg, of, refl, betas);
     }
     count_launch(1);

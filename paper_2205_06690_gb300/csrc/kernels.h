@@ -24,6 +24,8 @@ template <typename T> struct GridTables {
 
 // Number of kernel launches issued by the library in this process (sbse_api.cu).
 void count_launch(int n);
+// raise (never lower) a kernel's dynamic shared memory limit to `bytes`, thread-safe
+void raise_smem_limit(const void *fn, size_t bytes);
 
 // ---- register-pencil three-pass round trip (fft_fast.cu), for the sizes fast_supported<T>(N)
 int upload_reg_twiddles();
@@ -148,14 +150,16 @@ template <typename T> void launch_half_phase(const GridTables<T> &g, C2<T> *a, C
 // cleaning of Eq. (15): overlaps O[c][s] = dV sum_r phi_s d_c (c < P*L complex columns)
 // use_tc (FP32 only): overlaps on the tensor cores; *err set on a timed-out tensor-core wait;
 // dens != null: the renormalisation also writes the induced density of each pair (Eq. 11)
-// phi_can != null (FP32 only): the projection update on the tensor cores from pre-split orbitals.
+// phi_can != null (FP32 only): the projection update on the tensor cores from pre-split orbitals;
+// phi_ov != null (FP32 only): the overlaps by the streamed tensor-core kernel from pre-split orbitals.
 // Returns c - 1 per orbital (device, P L values inside work); d is left unscaled: the next forward
 // pre-operation applies d <- c d + (c - 1) eta0 (XfwdArgs::cm1), and dens (P n_g) receives the
 // induced densities of the rescaled orbitals.
 template <typename T> const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ,
                                                  const C2<T> *a, C2<T> *d, int P, int L, const double *n0,
                                                  double dV, double *work, size_t work_bytes, bool use_tc,
-                                                 const uint8_t *phi_can, int *err, cudaStream_t s, T *dens);
+                                                 const uint8_t *phi_can, int *err, cudaStream_t s, T *dens,
+                                                 const uint8_t *phi_ov = nullptr);
 template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, int L);
 // d64 -> T conversion and FP64 -> T copies
 template <typename T> void launch_convert(const double *src, T *dst, long long n, cudaStream_t s);
@@ -181,6 +185,17 @@ size_t umma_prod_gemm_work_bytes(int M, int Nn, long long ng);
 int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const float *phi, int n_occ,
                               long long ng, double scale, double *out, double *work, int *err,
                               cudaStream_t s);
+
+// cleaning overlaps, streamed form (warp-specialised: bulk copies of raw d rows and of pre-split phi
+// slabs, BF16 split in shared memory, tcgen05 MMAs over a ring of stages): same result layout as
+// launch_umma_clean_overlap. phi_t holds phi as pre-split B tiles (umma_prepare_ov_phi, once per
+// propagation). Usable when umma_clean_ov_supported (n_occ <= 512, even point count).
+int launch_umma_clean_ov(const float *d_interleaved, int n_cols, const uint8_t *phi_t, int n_occ, long long ng,
+                         double scale, double *out, double *work, int *err, cudaStream_t s);
+bool umma_clean_ov_supported(int n_occ, long long ng);
+size_t umma_clean_ov_work_bytes(int n_cols, int n_occ, long long ng);
+size_t umma_ov_phi_bytes(long long ng, int n_occ);
+void umma_prepare_ov_phi(const float *phi, int n_occ, long long ng, uint8_t *out, cudaStream_t s);
 
 // cleaning update on the tensor cores: d_c -= sum_s O[2c+h][s] phi_s (h = re / im parts), plus
 // per-tile norm partials npart[tile][c][2] (tiles of umma_clean_update_tiles(ng) rows). phi_can holds

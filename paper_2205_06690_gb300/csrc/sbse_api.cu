@@ -26,6 +26,17 @@ void init_fft_kernels();
 void set_thread_error(const std::string &msg) { g_create_error = msg; }
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// The dynamic shared memory limit is an attribute of the kernel, shared by every context and host
+// thread: lowering it for one launch could make another thread's larger launch of the same kernel
+// fail in between. So it is only ever raised, under a lock.
+void raise_smem_limit(const void *fn, size_t bytes) {
+  static std::mutex mx;
+  static std::unordered_map<const void *, size_t> cur;
+  std::lock_guard<std::mutex> lk(mx);
+  size_t &c = cur[fn];
+  if (bytes > c && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    c = bytes;
+}
 }
 
 using namespace sbse;
@@ -35,6 +46,13 @@ namespace {
 struct DevBuf {
   void *p = nullptr;
   size_t cap = 0;
+};
+
+// scratch slots of a context
+enum Ws {
+  WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
+  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX,
+  WS_LOC, WS_DBLK, WS_MIX, WS_PHIOV, WS_COUNT
 };
 
 struct PhaseClock {
@@ -77,7 +95,7 @@ struct sbse_ctx {
   bool have_A = false;
   bool dab_given = false;  // the direct term's D columns were set by sbse_set_direct (in WS_DAB)
   // scratch
-  DevBuf ws[24];
+  DevBuf ws[WS_COUNT];
   int *flag = nullptr;
   // mixed mode: grid-sum contractions on the tensor cores (SBSE_OPT_TENSOR_CORES)
   int tensor_cores = 1;
@@ -103,11 +121,6 @@ struct sbse_ctx {
 };
 
 namespace {
-
-enum Ws {
-  WS_A0 = 0, WS_A1, WS_D, WS_U, WS_DN, WS_PW, WS_WACC, WS_N0, WS_PART, WS_CLEAN, WS_COEF,
-  WS_IDX, WS_GEMM, WS_K, WS_DAB, WS_EIG, WS_ACC32, WS_EM1, WS_QUEUE, WS_PHICAN, WS_SPEC, WS_FBOX, WS_LOC, WS_DBLK, WS_MIX
-};
 
 int fail(sbse_ctx *c, int code, const std::string &msg) {
   c->err = msg;
@@ -530,11 +543,16 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   if ((rc = ensure(ctx, WS_CLEAN, cw, &vp))) return rc;
   cwork = (double *)vp;
   // tensor-core cleaning update (FP32): the occupied orbitals as pre-split operand tiles
-  const uint8_t *phi_can = nullptr;
+  const uint8_t *phi_can = nullptr, *phi_ov = nullptr;
   if (sizeof(T) == sizeof(float) && ctx->tensor_cores) {
     if ((rc = ensure(ctx, WS_PHICAN, umma_update_phi_bytes(ng, ctx->n_occ), &vp))) return rc;
     umma_prepare_update_phi(ctx->phi32, ctx->n_occ, ng, (uint8_t *)vp, st);
     phi_can = (const uint8_t *)vp;
+    if (umma_clean_ov_supported(ctx->n_occ, ng) && p->clean_every > 0) {
+      if ((rc = ensure(ctx, WS_PHIOV, umma_ov_phi_bytes(ng, ctx->n_occ), &vp))) return rc;
+      umma_prepare_ov_phi(ctx->phi32, ctx->n_occ, ng, (uint8_t *)vp, st);
+      phi_ov = (const uint8_t *)vp;
+    }
   }
   if ((rc = ensure(ctx, WS_COEF, coef_host.size() * sizeof(double), &vp))) return rc;
   coef = (double *)vp;
@@ -654,7 +672,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       pending = false;
       // the renormalisation is applied by this step's forward pre-operation (one sweep of d less)
       cm1_pending = launch_clean<T>(g, phi_T<T>(ctx), ctx->n_occ, acur, d, P, L, n0, ctx->dV, cwork, cw,
-                                    ctx->tensor_cores != 0, phi_can, ctx->flag, st, dn);
+                                    ctx->tensor_cores != 0, phi_can, ctx->flag, st, dn, phi_ov);
       CHECK_LAUNCH("clean");
       if ((rc = poisson<T>(ctx, g, dn, P, pw, nullptr, accT, wts[n], em1, 0.5 * p->dt))) return rc;
       clk_end(ctx, ck);

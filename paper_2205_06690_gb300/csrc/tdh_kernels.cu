@@ -10,6 +10,8 @@
 #include <math.h>
 
 #include "gemm_nt.cuh"
+#include <algorithm>
+
 #include "kernels.h"
 #include "passes.cuh"
 
@@ -634,7 +636,8 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
   const long long chunks = (ng + kc - 1) / kc;
   const long long ptb = (ng + kUpPts - 1) / kUpPts;
   size_t b = 0;
-  const size_t tc_part = umma_prod_gemm_work_bytes((int)(2 * n_cols), n_occ, ng);
+  const size_t tc_part = std::max(umma_prod_gemm_work_bytes((int)(2 * n_cols), n_occ, ng),
+                                  umma_clean_ov_work_bytes((int)n_cols, n_occ, ng));
   const size_t simt_part = (size_t)(chunks * n_cols * n_occ * 2) * sizeof(double);
   b += simt_part > tc_part ? simt_part : tc_part;                 // overlap partials
   b += (size_t)(n_cols * n_occ * 2) * sizeof(double);           // overlaps
@@ -649,20 +652,24 @@ template <typename T> size_t clean_work_bytes(long long ng, int n_occ, int P, in
 template <typename T>
 const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, const C2<T> *a, C2<T> *d,
                            int P, int L, const double *n0, double dV, double *work, size_t work_bytes,
-                           bool use_tc, const uint8_t *phi_can, int *err, cudaStream_t s, T *dens) {
+                           bool use_tc, const uint8_t *phi_can, int *err, cudaStream_t s, T *dens,
+                           const uint8_t *phi_ov) {
   (void)work_bytes;
   const int n_cols = P * L;
   const long long kc = gemm_kchunk(g.ng);
   const long long chunks = (g.ng + kc - 1) / kc;
   const long long ptb = (g.ng + kUpPts - 1) / kUpPts;
   double *part = work;
-  const size_t tc_part = umma_prod_gemm_work_bytes(2 * n_cols, n_occ, g.ng) / sizeof(double);
+  const size_t tc_part = std::max(umma_prod_gemm_work_bytes(2 * n_cols, n_occ, g.ng),
+                                  umma_clean_ov_work_bytes(n_cols, n_occ, g.ng)) / sizeof(double);
   const size_t simt_part = (size_t)(chunks * n_cols * n_occ * 2);
   double *ov = part + (simt_part > tc_part ? simt_part : tc_part);
   double *npart = ov + (long long)n_cols * n_occ * 2;
   double *sums = npart + ptb * n_cols * 2;
   double *cm1 = sums + (long long)n_cols * 2;
-  if (use_tc && sizeof(T) == sizeof(float)) {
+  if (phi_ov && sizeof(T) == sizeof(float)) {
+    launch_umma_clean_ov(reinterpret_cast<const float *>(d), n_cols, phi_ov, n_occ, g.ng, dV, ov, part, err, s);
+  } else if (use_tc && sizeof(T) == sizeof(float)) {
     launch_umma_clean_overlap(reinterpret_cast<const float *>(d), n_cols,
                               reinterpret_cast<const float *>(phi_occ), n_occ, g.ng, dV, ov, part, err, s);
   } else {
@@ -775,7 +782,7 @@ void init_fft_kernels() {
                                      cudaStream_t);                                              \
   template const double *launch_clean<T>(const GridTables<T> &, const T *, int, const C2<T> *,      \
                                          C2<T> *, int, int, const double *, double, double *, size_t, \
-                                         bool, const uint8_t *, int *, cudaStream_t, T *);                                                     \
+                                         bool, const uint8_t *, int *, cudaStream_t, T *, const uint8_t *); \
   template size_t clean_work_bytes<T>(long long, int, int, int);                                   \
   template void launch_convert<T>(const double *, T *, long long, cudaStream_t);
 

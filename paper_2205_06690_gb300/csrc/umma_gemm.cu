@@ -551,7 +551,7 @@ void launch_umma_clean_update(const double *ov, int n_cols, const uint8_t *phi_c
   k_canon_tiles<kUmM, SrcRowsF64><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
       SrcRowsF64{ov, M, n_occ}, m_tiles, kchunks(n_occ), o_can);
   const size_t smem = (size_t)kCanA + kCanB;
-  cudaFuncSetAttribute(k_umma_clean_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void *)k_umma_clean_update, smem);
   dim3 grid((unsigned)umma_clean_update_tiles(ng), (unsigned)m_tiles);
   k_umma_clean_update<<<grid, kUmThreads, smem, s>>>(o_can, M, phi_can, kchunks(n_occ), ng, d_interleaved,
                                                      a_interleaved, L, npart, err);
@@ -589,7 +589,7 @@ static int launch_umma(const float *F, const int2 *xi, int M, const float *Y, in
   const long long kc = umma_kchunk(ng, tiles);
   const long long chunks = (ng + kc - 1) / kc;
   const size_t smem = kUmStages * umma_stage_bytes(nt);
-  cudaFuncSetAttribute(k_umma_prod_gemm<AMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void *)k_umma_prod_gemm<AMODE>, smem);
   dim3 grid((unsigned)chunks, (M + kUmM - 1) / kUmM, (Nn + nt - 1) / nt);
   k_umma_prod_gemm<AMODE><<<grid, kPgThreads, smem, s>>>(F, xi, M, Y, Nn, nt, ng, kc, work, err);
   count_launch(1);
@@ -608,6 +608,320 @@ int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const floa
                               cudaStream_t s) {
   return launch_umma<UA_COMPLEX>(d_interleaved, nullptr, 2 * n_cols, phi, n_occ, ng, scale, out, work,
                                  err, s);
+}
+
+
+// ---- cleaning overlaps, streamed form ----------------------------------------------------------
+// ov[2c + h][s] = sum_r (Re, Im)_h d_c(r) phi_s(r) (Eq. 15) with the grid points as the contraction
+// index. One CTA owns 64 complex columns of d (128 accumulator rows: real and imaginary part of each
+// column) times every occupied state (up to 512 accumulator columns in tensor memory), over a chunk
+// of grid points. Warp roles:
+//   warp 4     bulk copies: the raw interleaved FP32 d rows of a 32-point stage (one copy per
+//              column) and the stage's slab of pre-split phi tiles (one copy), on one mbarrier;
+//   warps 0-3  split the raw stage into BF16 hi / lo rows 2c, 2c + 1 of the A tile (shared memory
+//              to shared memory), then, after the last stage, read the accumulator (one TMEM lane
+//              quarter each) and write the FP64 partials of the chunk;
+//   warp 5     allocates tensor memory and issues the MMAs (hi*hi + hi*lo + lo*hi per 16 points,
+//              N split into pieces of at most 256), committing each stage to its `empty` barrier.
+// A ring of S stages keeps copies, splits and MMAs of successive stages in flight together. Every
+// wait is bounded; a role that gives up raises a shared abort flag (the others then stop waiting)
+// and *err, and the copies and MMAs already issued are waited for before memory is released.
+constexpr int kOvKS = 32;                           // grid points per stage
+constexpr int kOvCols = kUmM / 2;                   // complex columns of d per CTA
+constexpr int kOvRawLd = kOvKS * 8 + 16;            // bytes per raw column in shared memory (padded)
+constexpr unsigned kOvRaw = kOvCols * kOvRawLd;     // 17408
+constexpr unsigned kOvA = 2u * kUmM * kOvKS * 2;    // hi + lo A tile: 16384
+constexpr int kOvThreads = 192;
+constexpr int kOvMaxStages = 8;
+constexpr size_t kOvSmemBudget = 200u * 1024u;
+
+__host__ __device__ constexpr unsigned ov_b_bytes(int nb) { return 2u * (unsigned)nb * kOvKS * 2; }
+__host__ __device__ constexpr unsigned ov_stage_bytes(int nb) { return kOvRaw + kOvA + ov_b_bytes(nb); }
+
+// offset of element (row, core matrix kc) in an R x 32 BF16 tile, canonical K-major, no swizzle:
+// K-adjacent core matrices 128 B apart, 8-row groups 512 B apart
+__device__ __forceinline__ uint32_t canon32_off(int row, int kc) {
+  return (uint32_t)(((row >> 3) * (kOvKS / 8) + kc) * 128 + (row & 7) * 16);
+}
+
+// accumulator rows (padded occupied count) of the streamed overlaps: a multiple of 16
+static int ov_rows(int n_occ) { return ((n_occ + 15) / 16) * 16; }
+
+// phi as the B operand of the streamed overlaps: per 32-point stage a slab of hi then lo tiles of
+// ov_rows(n_occ) rows (zero beyond n_occ and beyond the last grid point)
+size_t umma_ov_phi_bytes(long long ng, int n_occ) {
+  return (size_t)((ng + kOvKS - 1) / kOvKS) * ov_b_bytes(ov_rows(n_occ));
+}
+
+__global__ void k_ov_phi_tiles(const float *phi, int n_occ, int nb, long long ng, long long n_ks, uint8_t *out) {
+  // thread per (row, stage, group of 8 points); groups fastest, so a warp reads a row contiguously
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per_row = n_ks * (kOvKS / 8);
+  if (t >= (long long)nb * per_row) return;
+  const int row = (int)(t / per_row);
+  const long long rem = t - (long long)row * per_row;
+  const long long ks = rem / (kOvKS / 8);
+  const int g = (int)(rem - ks * (kOvKS / 8));
+  const long long p0 = ks * kOvKS + g * 8;
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (row < n_occ && p0 + j < ng) ? phi[(long long)row * ng + p0 + j] : 0.f;
+  uint4 hi, lo;
+  split8(x, &hi, &lo);
+  uint8_t *slab = out + (size_t)ks * ov_b_bytes(nb);
+  const uint32_t off = canon32_off(row, g);
+  *reinterpret_cast<uint4 *>(slab + off) = hi;
+  *reinterpret_cast<uint4 *>(slab + (size_t)nb * kOvKS * 2 + off) = lo;
+}
+
+void umma_prepare_ov_phi(const float *phi, int n_occ, long long ng, uint8_t *out, cudaStream_t s) {
+  const int nb = ov_rows(n_occ);
+  const long long n_ks = (ng + kOvKS - 1) / kOvKS;
+  const long long threads = (long long)nb * n_ks * (kOvKS / 8);
+  k_ov_phi_tiles<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(phi, n_occ, nb, ng, n_ks, out);
+  count_launch(1);
+}
+
+// bounded wait that also gives up when another role has raised the abort flag
+__device__ __forceinline__ bool ov_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  const uint32_t a = smem_u32(bar);
+  for (unsigned i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(a, parity)) return true;
+    if ((i & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void ov_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kOvThreads, 1)
+    k_umma_clean_ov(const float2 *d, int n_cols, const uint8_t *phi_t, int nb, int n_occ, long long ng,
+                    long long kchunk, int S, double *part, int *err) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[kOvMaxStages], conv[kOvMaxStages], empty[kOvMaxStages], accb;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  volatile int *abort_v = &abort_flag;
+  uint8_t *raw = smem;
+  uint8_t *atile = raw + (size_t)S * kOvRaw;
+  uint8_t *btile = atile + (size_t)S * kOvA;
+  const unsigned bbytes = ov_b_bytes(nb);
+  const int M = 2 * n_cols;
+  const int mt = blockIdx.x;  // m tile fastest: the CTAs that share a chunk's phi slabs run together
+  const int c0 = mt * kOvCols;
+  const int ncols_t = min(kOvCols, n_cols - c0);
+  const long long kbeg = (long long)blockIdx.y * kchunk;
+  const long long kend = min(kbeg + kchunk, ng);
+  const int n_iter = kend > kbeg ? (int)((kend - kbeg + kOvKS - 1) / kOvKS) : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tcols = 32;
+  while (tcols < nb) tcols <<= 1;
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&conv[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accb)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  int issued = 0;  // bulk-copy stages issued (warp 4)
+  if (warp == 4) {
+    // ---- bulk copies
+    for (int it = 0; it < n_iter; ++it) {
+      const int s = it % S;
+      bool ok = true;
+      if (it >= S) ok = ov_wait(&empty[s], (uint32_t)((it / S - 1) & 1), abort_v);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) { *abort_v = 1; atomicExch(err, 1); }
+        break;
+      }
+      const long long k0 = kbeg + (long long)it * kOvKS;
+      const int npts = (int)min((long long)kOvKS, kend - k0);  // even: ng and k0 are
+      if (lane == 0) tma_bar_expect(&full[s], (unsigned)ncols_t * npts * 8u + bbytes);
+      __syncwarp();
+      for (int c = lane; c < ncols_t; c += 32)
+        tma_load_1d(raw + (size_t)s * kOvRaw + c * kOvRawLd, d + (long long)(c0 + c) * ng + k0, npts * 8u, &full[s]);
+      if (lane == 0) tma_load_1d(btile + (size_t)s * bbytes, phi_t + (size_t)(k0 / kOvKS) * bbytes, bbytes, &full[s]);
+      ++issued;
+    }
+  } else if (warp == 5) {
+    // ---- MMA issue
+    if (lane == 0) {
+      for (int it = 0; it < n_iter; ++it) {
+        const int s = it % S;
+        if (!ov_wait(&conv[s], (uint32_t)((it / S) & 1), abort_v)) {
+          *abort_v = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ah = smem_u32(atile + (size_t)s * kOvA), al = ah + kUmM * kOvKS * 2;
+        const uint32_t bh = smem_u32(btile + (size_t)s * bbytes), bl = bh + (uint32_t)nb * kOvKS * 2;
+#pragma unroll
+        for (int t = 0; t < kOvKS / 16; ++t) {
+          const uint32_t o = t * 256;
+          const uint64_t dah = make_desc(ah + o, 128, 512), dal = make_desc(al + o, 128, 512);
+          const uint32_t acc = (it > 0 || t > 0) ? 1u : 0u;
+          for (int n0 = 0; n0 < nb; n0 += 256) {
+            const int nn = min(256, nb - n0);
+            const uint32_t idesc = make_idesc(kUmM, nn);
+            const uint32_t boff = (uint32_t)(n0 / 8) * 512u + o;
+            const uint64_t dbh = make_desc(bh + boff, 128, 512), dbl = make_desc(bl + boff, 128, 512);
+            mma_bf16(tmem + (uint32_t)n0, dah, dbh, idesc, acc);
+            mma_bf16(tmem + (uint32_t)n0, dah, dbl, idesc, 1u);
+            mma_bf16(tmem + (uint32_t)n0, dal, dbh, idesc, 1u);
+          }
+        }
+        mma_commit(smem_u32(&empty[s]));
+      }
+      mma_commit(smem_u32(&accb));  // arrives once every MMA issued above has completed
+    }
+  } else {
+    // ---- split the raw stage into the A tile (warps 0-3, 128 threads)
+    const int t = threadIdx.x;
+    for (int it = 0; it < n_iter; ++it) {
+      const int s = it % S;
+      const bool ok = ov_wait(&full[s], (uint32_t)((it / S) & 1), abort_v);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) { *abort_v = 1; atomicExch(err, 1); }
+        break;
+      }
+      const long long k0 = kbeg + (long long)it * kOvKS;
+      const int npts = (int)min((long long)kOvKS, kend - k0);
+      const uint8_t *rs = raw + (size_t)s * kOvRaw;
+      uint8_t *ahi = atile + (size_t)s * kOvA, *alo = ahi + kUmM * kOvKS * 2;
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        const int col = t & (kOvCols - 1), g = (t >> 6) + 2 * pass;
+        float re[8], im[8];
+        if (col < ncols_t && g * 8 + 8 <= npts) {
+          const float4 *src = reinterpret_cast<const float4 *>(rs + col * kOvRawLd + g * 64);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 v = src[q];
+            re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
+          }
+        } else {
+          const float2 *src = reinterpret_cast<const float2 *>(rs + col * kOvRawLd + g * 64);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const bool in = col < ncols_t && g * 8 + j < npts;
+            const float2 v = in ? src[j] : make_float2(0.f, 0.f);
+            re[j] = v.x;
+            im[j] = v.y;
+          }
+        }
+        uint4 hi, lo;
+        split8(re, &hi, &lo);
+        *reinterpret_cast<uint4 *>(ahi + canon32_off(2 * col, g)) = hi;
+        *reinterpret_cast<uint4 *>(alo + canon32_off(2 * col, g)) = lo;
+        split8(im, &hi, &lo);
+        *reinterpret_cast<uint4 *>(ahi + canon32_off(2 * col + 1, g)) = hi;
+        *reinterpret_cast<uint4 *>(alo + canon32_off(2 * col + 1, g)) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+      __syncwarp();
+      if (lane == 0) ov_arrive(&conv[s]);
+    }
+    // ---- epilogue: accumulator lane quarter `warp`, FP64 partials of this chunk
+    bool ok = n_iter > 0 && __all_sync(0xffffffffu, ov_wait(&accb, 0u, abort_v)) && !*abort_v;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int m = mt * kUmM + warp * 32 + lane;
+    double *o = part + ((long long)blockIdx.y * M + m) * n_occ;
+    if (ok) {
+      for (int c = 0; c < nb; c += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c + j < n_occ) o[c + j] = (double)__uint_as_float(r[j]);
+        }
+      }
+    } else if (n_iter == 0 && m < M) {
+      for (int c = 0; c < n_occ; ++c) o[c] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (*abort_v) {
+    // an abandoned pipeline: every issued copy has landed and every issued MMA has completed
+    // before shared and tensor memory are released (bounded waits again)
+    if (warp == 4 && lane == 0)
+      for (int s = 0; s < S && s < issued; ++s) {
+        const int last = issued - 1 - ((issued - 1 - s) % S);  // last iteration that used slot s
+        mbar_wait(smem_u32(&full[s]), (uint32_t)((last / S) & 1));
+      }
+    if (warp == 5 && lane == 0) mbar_wait(smem_u32(&accb), 0u);
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
+// grid of the streamed overlaps: (m tiles, chunks); about one CTA per SM, whole stages per chunk
+static void ov_grid(int n_cols, long long ng, int *m_tiles, long long *kc, long long *chunks) {
+  *m_tiles = (n_cols + kOvCols - 1) / kOvCols;
+  long long target = 152 / *m_tiles;
+  if (target < 1) target = 1;
+  long long c = (ng + target - 1) / target;
+  c = ((c + kOvKS - 1) / kOvKS) * kOvKS;
+  *kc = c;
+  *chunks = (ng + c - 1) / c;
+}
+
+static int ov_stages(int nb) {
+  int s = (int)(kOvSmemBudget / ov_stage_bytes(nb));
+  return s > kOvMaxStages ? kOvMaxStages : s;
+}
+
+bool umma_clean_ov_supported(int n_occ, long long ng) {
+  const int nb = ov_rows(n_occ);
+  return nb <= 512 && (ng % 2) == 0 && ov_stages(nb) >= 2;
+}
+
+size_t umma_clean_ov_work_bytes(int n_cols, int n_occ, long long ng) {
+  int mt;
+  long long kc, chunks;
+  ov_grid(n_cols, ng, &mt, &kc, &chunks);
+  return (size_t)(chunks * 2 * n_cols * n_occ) * sizeof(double);
+}
+
+int launch_umma_clean_ov(const float *d_interleaved, int n_cols, const uint8_t *phi_t, int n_occ, long long ng,
+                         double scale, double *out, double *work, int *err, cudaStream_t s) {
+  const int nb = ov_rows(n_occ);
+  const int S = ov_stages(nb);
+  int mt;
+  long long kc, chunks;
+  ov_grid(n_cols, ng, &mt, &kc, &chunks);
+  const size_t smem = (size_t)S * ov_stage_bytes(nb);
+  raise_smem_limit((const void *)k_umma_clean_ov, smem);
+  dim3 grid((unsigned)mt, (unsigned)chunks);
+  k_umma_clean_ov<<<grid, kOvThreads, smem, s>>>(reinterpret_cast<const float2 *>(d_interleaved), n_cols, phi_t,
+                                                 nb, n_occ, ng, kc, S, work, err);
+  count_launch(1);
+  launch_reduce_cols(work, (int)chunks, 2 * n_cols * n_occ, scale, out, s);
+  return 0;
 }
 
 }  // namespace sbse
