@@ -204,12 +204,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_SOURCES = ["fft_fast.cu", "fft_split.cu", "fft_reg.cuh", "passes.cuh", "tma.cuh", "common.cuh", "kernels.h"]
+# the sources the pass kernels of each workload are compiled from (their definitions and the data
+# structures they read; declarations of other launchers do not enter)
+KERNEL_SOURCES = {
+    "large96": ["fft_split.cu", "fft_reg.cuh", "passes.cuh", "common.cuh", "tables.cuh"],
+    "default": ["fft_fast.cu", "fft_reg.cuh", "passes.cuh", "tma.cuh", "common.cuh", "tables.cuh"],
+}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(workload: str = "default") -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES.get(workload, KERNEL_SOURCES["default"]):
         with open(os.path.join(ROOT, "paper_2205_06690_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -223,7 +228,7 @@ def profiled_traffic(phase, workload, mixed):
         return None, None
     with open(path) as f:
         d = json.load(f)
-    if d.get("source_sha256_16") != kernel_source_hash():
+    if d.get("source_sha256_16") != kernel_source_hash(workload):
         return None, "kernel sources changed since the ncu capture"
     v = d.get("dram_bytes_per_launch", {}).get(str(phase))
     return (float(v), os.path.relpath(path, ROOT)) if v else (None, None)

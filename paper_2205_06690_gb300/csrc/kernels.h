@@ -5,22 +5,9 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "tables.cuh"
 
 namespace sbse {
-
-// Device tables of one grid, in working precision T.
-template <typename T> struct GridTables {
-  int N = 0;
-  long long ng = 0;
-  FftPlan plan{};
-  C2<T> *tw = nullptr;      // exp(-2 pi i k / N), k < N
-  C2<T> *kin = nullptr;     // exp(-i k_m^2 dt / 2) per axis index m (rebuilt per dt); for even N
-                            // followed by the lane-pair round-trip multipliers Kp, M1, M2 (N/2 each)
-  T *k2 = nullptr;          // k_m^2 per axis index m
-  T *v_loc = nullptr;       // V_loc(r), ng
-  C2<T> *pv_dt = nullptr;   // exp(-i V_loc dt), ng (rebuilt per dt)
-  C2<T> *pv_half = nullptr; // exp(-i V_loc dt / 2), ng
-};
 
 // Number of kernel launches issued by the library in this process (sbse_api.cu).
 void count_launch(int n);
@@ -36,29 +23,8 @@ int upload_split_twiddles();
 void init_split_kernels();
 template <typename T> bool fast_supported(int N);
 template <typename T> void init_fast_kernels();
-template <typename T> struct XfwdArgs;
-template <typename T> struct GridTables;
 
 // ---- FFT passes (tdh_kernels.cu). Items are contiguous arrays of ng complex values.
-struct PoissonOut;
-enum XfwdMode { XF_PHASE_A = 0, XF_PHASE_PAIR = 1, XF_PACK_DN = 2, XF_PACK_PROD = 3 };
-
-template <typename T> struct XfwdArgs {
-  int mode;
-  int n_items;           // orbitals (A: L, PAIR: P*L) or Poisson slots
-  const C2<T> *in;       // A: a_cur; PAIR: d (in place)
-  C2<T> *out;            // A: a_next; PAIR: d; PACK: packed work buffer
-  const C2<T> *a;        // PAIR: a_cur
-  const C2<T> *pv;       // A, PAIR: exp(-i V_loc tau) per grid point (tau = dt or dt/2)
-  const C2<T> *em1;      // PAIR: exp(-i u tau) - 1 per pair (ng each); null -> u ignored
-  const double *cm1;     // PAIR: c - 1 per orbital of a renormalisation still to apply (null: none)
-  int L;                 // PAIR: orbitals per pair
-  const T *dn;           // PACK_DN: density per pair; slot s packs 2s (re) and 2s+1 (im)
-  int n_dn;              // PACK_DN: number of densities
-  const T *orb;          // PACK_PROD: orbital rows (ng each)
-  const int4 *prod;      // PACK_PROD: per slot (i1, j1, i2, j2); i2 < 0 -> imaginary part 0
-};
-
 template <typename T> void launch_xfwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
 template <typename T> void launch_plane_fwd(const GridTables<T> &g, const XfwdArgs<T> &a, cudaStream_t s);
 // tma_err != null (FP32, N in 32 / 40 / 48 / 64): the bulk-copy streamed column kernel
@@ -69,14 +35,6 @@ template <typename T> void launch_zcol(const GridTables<T> &g, C2<T> *d, int n_i
 template <typename T> void launch_plane_inv_orb(const GridTables<T> &g, C2<T> *d, int n_items,
                                                 const C2<T> *a_next, int L, T *dens, cudaStream_t s,
                                                 int *tma_err = nullptr);
-// Poisson epilogue outputs of slot pair k: u_out[k] = u, acc[k] (+)= coef u, and, when em1_out is
-// not null, em1_out[k] = exp(-i u tau_next) - 1 = -2i sin(u tau_next/2) exp(-i u tau_next/2), the
-// potential factor of the next split-operator step.
-struct PoissonOut {
-  int n_out;
-  double coef, keep;
-  double tau_next;
-};
 template <typename T> void launch_plane_inv_poisson(const GridTables<T> &g, C2<T> *d, int n_slots,
                                                     const PoissonOut &po, T *u_out, T *acc,
                                                     C2<T> *em1_out, cudaStream_t s);
@@ -96,9 +54,6 @@ template <typename T> void launch_phase_table(const double *v64, long long ng, d
                                               cudaStream_t s);
 template <typename T> void launch_ypass(const GridTables<T> &g, C2<T> *data, int n_items, int sign,
                                         cudaStream_t s);
-// multiplier of the z pass: kinetic propagator, Coulomb kernel 4 pi / |G|^2 (G = 0 dropped), or the
-// kinetic energy |G|^2 / 2 (the spectral -1/2 Laplacian); each with the 1/N^3 of the round trip
-enum ZMult { Z_KINETIC = 0, Z_POISSON = 1, Z_HALF_G2 = 2 };
 template <typename T> void launch_zpass(const GridTables<T> &g, C2<T> *data, int n_items, int mult,
                                         cudaStream_t s);
 // inverse x pass of orbitals; with dens != nullptr, items are grouped L per pair and the induced
@@ -114,20 +69,7 @@ template <typename T> void launch_xinv_poisson(const GridTables<T> &g, C2<T> *da
 // acc64 += acc, acc = 0
 template <typename T> void launch_flush_acc(double *acc64, T *acc, long long n, cudaStream_t s);
 
-// ---- persistent split-operator step (fft_fast.cu): tile queue and completion counters
-enum StepItemKind { SI_A_FWD = 0, SI_A_Z = 1, SI_A_INV = 2, SI_P_FWD = 3, SI_P_Z = 4, SI_P_INV = 5 };
-struct StepQueue {
-  const int4 *items;    // {kind, orbital (or pair for SI_P_INV), tile, 0}, dependency-ordered
-  int n_items;
-  unsigned *claim;      // claim counter, monotonic over the launches of one sbse_apply_W
-  unsigned claim_base;  // its value when this launch starts
-  unsigned *a_fwd, *a_z;  // per eta0 orbital
-  unsigned *a_inv;        // all eta0 inverse tiles
-  unsigned *p_fwd, *p_z;  // per pair orbital
-  unsigned epoch;         // launch index: completion targets are (epoch + 1) x tiles
-  int *err;               // set when a bounded wait times out
-  unsigned wait_limit;    // iterations of each bounded wait (about 100 ns each)
-};
+// ---- persistent split-operator step (fft_fast.cu; its tile queue StepQueue is in tables.cuh)
 template <typename T>
 void launch_step_persistent(const GridTables<T> &g, const XfwdArgs<T> &fa, const XfwdArgs<T> &fp,
                             C2<T> *a_next, C2<T> *d, T *dens, int L, const StepQueue &q, int grid,

@@ -68,6 +68,10 @@ PRESETS = {
                     n_steps=1000, gamma=0.1, n_exc=10),
     "large96": Preset("large96", N=96, box=24.0, n_wells=170, seed=2, n_occ=260, n_o=16,
                       n_c=32, n_steps=2000, gamma=0.1, n_exc=10),
+    # the 96^3 grid with fewer states (about 2 GB on the device): kernel-profiler captures of the
+    # 96^3 pass kernels, whose work per orbital is that of large96
+    "prof96": Preset("prof96", N=96, box=24.0, n_wells=40, seed=3, n_occ=60, n_o=4, n_c=8,
+                     n_steps=2000, gamma=0.1, n_exc=4),
 }
 
 

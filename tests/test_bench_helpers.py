@@ -8,6 +8,7 @@ import bench
 def test_traffic_follows_the_recorded_kernel_sources(tmp_path, monkeypatch):
     h = bench.kernel_source_hash()
     assert len(h) == 16 and h == bench.kernel_source_hash()
+    assert bench.kernel_source_hash("large96") != h  # the 96^3 passes are built from other sources
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "pair_passes_w_traffic.txt").write_text(json.dumps(
@@ -15,7 +16,7 @@ def test_traffic_follows_the_recorded_kernel_sources(tmp_path, monkeypatch):
     (prof / "pair_passes_old_traffic.txt").write_text(json.dumps(
         {"source_sha256_16": "0" * 16, "dram_bytes_per_launch": {"5": 123}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda workload="default": h)
     assert bench.profiled_traffic(5, "w", True) == (123.0, "profiles/pair_passes_w_traffic.txt")
     assert bench.profiled_traffic(6, "w", True) == (None, None)
     assert bench.profiled_traffic(5, "w", False) == (None, None)
