@@ -369,6 +369,21 @@ int sbse_fno_pair_inputs(sbse_ctx *ctx, int n_pairs, const int *pi, const int *p
 int sbse_surrogate_W(sbse_ctx *ctx, sbse_fno *fno, int n_pairs, const int *pi, const int *pj, double s_rho,
                      double s_v, double s_w);
 
+/* Bare potentials q_ij = v (phi_i phi_j) (FP64 Poisson, the first term of W_ij = q_ij + W^pol_ij,
+ * Sec. II.B) stored as the W of the given pairs of the valence window, as a starting point for a
+ * polarisation part added by sbse_add_W. Errors: INVALID_ARG (indices, duplicates), NOT_READY, OOM,
+ * CUDA. */
+int sbse_bare_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj);
+/* W_ij += scale * y_k for the k-th pair (i, j): y_dev is a DEVICE array [n_pairs][n^3] of FP32 fields
+ * on ctx's grid (for example the surrogate's W^pol). The pairs' W must be available (sbse_bare_W or
+ * sbse_apply_W). Errors: INVALID_ARG, NOT_READY, CUDA. */
+int sbse_add_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, const float *y_dev, double scale);
+/* Periodic trilinear resampling of `count` FP32 fields (DEVICE arrays, [count][n^3], x fastest) from an
+ * n_src^3 grid onto an n_dst^3 grid of the same box (point i of the new grid at i n_src / n_dst old
+ * grid units), on ctx's stream; src and dst must not overlap. Connects the surrogate's grid to a
+ * system's grid. Errors: INVALID_ARG, CUDA. */
+int sbse_resample(sbse_ctx *ctx, int count, int n_src, const float *src_dev, int n_dst, float *dst_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -130,6 +130,9 @@ def load() -> C.CDLL:
         "sbse_fno_train_step": (i, [vp, i, vp, vp, C.c_float, dp]),
         "sbse_fno_pair_inputs": (i, [vp, i, ip, ip, d, d, vp]),
         "sbse_surrogate_W": (i, [vp, vp, i, ip, ip, d, d, d]),
+        "sbse_bare_W": (i, [vp, i, ip, ip]),
+        "sbse_add_W": (i, [vp, i, ip, ip, vp, d]),
+        "sbse_resample": (i, [vp, i, i, vp, i, vp]),
     })
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -242,6 +245,23 @@ def sbse_fno_pair_inputs(ctx, pairs, s_rho: float, s_v: float, x_ptr: int) -> No
 def sbse_surrogate_W(ctx, fno_handle, pairs, s_rho: float, s_v: float, s_w: float) -> None:
     pi, pj, a, b = _pairs_c(pairs)
     _check(ctx, load().sbse_surrogate_W(ctx, fno_handle, len(pairs), a, b, s_rho, s_v, s_w))
+
+
+def sbse_bare_W(ctx, pairs) -> None:
+    """W_ij = q_ij = v(phi_i phi_j) for the pairs (the bare part of W)."""
+    pi, pj, a, b = _pairs_c(pairs)
+    _check(ctx, load().sbse_bare_W(ctx, len(pairs), a, b))
+
+
+def sbse_add_W(ctx, pairs, y_ptr: int, scale: float) -> None:
+    """W_ij += scale * y[k] from a device array of FP32 fields on the context's grid."""
+    pi, pj, a, b = _pairs_c(pairs)
+    _check(ctx, load().sbse_add_W(ctx, len(pairs), a, b, C.c_void_p(y_ptr), scale))
+
+
+def sbse_resample(ctx, count: int, n_src: int, src_ptr: int, n_dst: int, dst_ptr: int) -> None:
+    """Periodic trilinear resampling of device FP32 fields between grids of the same box."""
+    _check(ctx, load().sbse_resample(ctx, count, n_src, C.c_void_p(src_ptr), n_dst, C.c_void_p(dst_ptr)))
 
 
 def sbse_build_A(ctx, terms: int = SBSE_EXCHANGE | SBSE_DIRECT, n: int | None = None):
@@ -392,7 +412,7 @@ class FNO:
         h = C.c_void_p()
         _fcheck(None, load().sbse_fno_create(C.byref(h), device, n, width, modes, layers, max_batch))
         self.h = h
-        self.n, self.width, self.modes, self.layers = n, width, modes, layers
+        self.n, self.width, self.modes, self.layers, self.max_batch = n, width, modes, layers, max_batch
         self.n_params = int(load().sbse_fno_num_params(h))
 
     def close(self):

@@ -32,6 +32,8 @@ int ctx_view(sbse_ctx *ctx, CtxView *v);
 int ctx_pair_slot(sbse_ctx *ctx, int i, int j);
 void ctx_mark_pair(sbse_ctx *ctx, int slot);
 void ctx_set_error(sbse_ctx *ctx, const std::string &m);
+bool ctx_have_pair(sbse_ctx *ctx, int slot);
+int ctx_device(sbse_ctx *ctx, int *device);
 }
 
 using namespace sbse;
@@ -312,6 +314,46 @@ __global__ void k_pair_inputs(const float *phi, const double *v, const int2 *st,
 __global__ void k_store_w(const float *y, double *W, long long ng, double s_w) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < ng) W[r] = s_w * (double)y[r];
+}
+
+// W slot += scale * y (FP32 field added to the FP64 screened potential)
+__global__ void k_add_w(const float *y, double *W, long long ng, double scale) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < ng) W[r] += scale * (double)y[r];
+}
+
+// periodic trilinear resampling of `count` fields from an ns^3 grid onto an nd^3 grid of the same
+// box (point i of the new grid sits at i ns / nd in old grid units; weights from the exact rational
+// position)
+__global__ void k_resample(const float *src, int ns, float *dst, int nd, long long total) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const long long nd3 = (long long)nd * nd * nd, ns3 = (long long)ns * ns * ns;
+  const long long fld = t / nd3;
+  long long r = t - fld * nd3;
+  const int ix = (int)(r % nd);
+  r /= nd;
+  const int iy = (int)(r % nd), iz = (int)(r / nd);
+  int i0[3], i1[3];
+  float w1[3];
+  const int id[3] = {ix, iy, iz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long p = (long long)id[a] * ns;
+    i0[a] = (int)(p / nd);
+    w1[a] = (float)(p - (long long)i0[a] * nd) / (float)nd;
+    i1[a] = i0[a] + 1 == ns ? 0 : i0[a] + 1;
+  }
+  const float *s = src + fld * ns3;
+  auto at = [&](int x, int y, int z) { return s[((long long)z * ns + y) * ns + x]; };
+  float acc = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+    const float w = (bx ? w1[0] : 1.f - w1[0]) * (by ? w1[1] : 1.f - w1[1]) * (bz ? w1[2] : 1.f - w1[2]);
+    if (w != 0.f) acc += w * at(bx ? i1[0] : i0[0], by ? i1[1] : i0[1], bz ? i1[2] : i0[2]);
+  }
+  dst[t] = acc;
 }
 
 // a[i] *= s[i % m]: the per-kx factor c_kx / N^3 of the spectral gradient (kx is the fastest mode index)
@@ -735,6 +777,43 @@ int sbse_surrogate_W(sbse_ctx *ctx, sbse_fno *f, int n_pairs, const int *pi, con
   cudaFreeAsync(y, f->stream);
   cudaStreamSynchronize(f->stream);
   return rc;
+}
+
+int sbse_add_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj, const float *y_dev, double scale) {
+  sbse::CtxView cv;
+  if (sbse::ctx_view(ctx, &cv) != SBSE_OK) return SBSE_ERR_NOT_READY;
+  if (!pi || !pj || !y_dev || n_pairs < 1 || !isfinite(scale)) return SBSE_ERR_INVALID_ARG;
+  std::vector<int> slots(n_pairs);
+  for (int k = 0; k < n_pairs; ++k) {
+    if (pi[k] < 0 || pj[k] < pi[k] || pj[k] >= cv.n_o) return SBSE_ERR_INVALID_ARG;
+    slots[k] = sbse::ctx_pair_slot(ctx, pi[k], pj[k]);
+    if (!sbse::ctx_have_pair(ctx, slots[k])) {
+      sbse::ctx_set_error(ctx, "sbse_add_W: W of a pair is not available (sbse_bare_W or sbse_apply_W first)");
+      return SBSE_ERR_NOT_READY;
+    }
+  }
+  if (cudaSetDevice(cv.device) != cudaSuccess) return SBSE_ERR_CUDA;
+  for (int k = 0; k < n_pairs; ++k) {
+    k_add_w<<<nblk(cv.ng), kT, 0, cv.stream>>>(y_dev + (long long)k * cv.ng, cv.W + (long long)slots[k] * cv.ng,
+                                               cv.ng, scale);
+    count_launch(1);
+    sbse::ctx_mark_pair(ctx, slots[k]);
+  }
+  return cudaStreamSynchronize(cv.stream) == cudaSuccess ? SBSE_OK : SBSE_ERR_CUDA;
+}
+
+int sbse_resample(sbse_ctx *ctx, int count, int n_src, const float *src_dev, int n_dst, float *dst_dev) {
+  if (!ctx || count < 1 || n_src < 1 || n_dst < 1 || !src_dev || !dst_dev || src_dev == dst_dev)
+    return SBSE_ERR_INVALID_ARG;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  if (sbse_get_stream(ctx, (void **)&st) != SBSE_OK || sbse::ctx_device(ctx, &device) != SBSE_OK)
+    return SBSE_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return SBSE_ERR_CUDA;
+  const long long total = (long long)count * n_dst * n_dst * n_dst;
+  k_resample<<<nblk(total), kT, 0, st>>>(src_dev, n_src, dst_dev, n_dst, total);
+  count_launch(1);
+  return cudaStreamSynchronize(st) == cudaSuccess ? SBSE_OK : SBSE_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -969,6 +969,12 @@ void ctx_mark_pair(sbse_ctx *ctx, int slot) {
   ctx->have_A = false;
 }
 void ctx_set_error(sbse_ctx *ctx, const std::string &m) { ctx->err = m; }
+bool ctx_have_pair(sbse_ctx *ctx, int slot) { return ctx->have[slot] != 0; }
+int ctx_device(sbse_ctx *ctx, int *device) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  *device = ctx->device;
+  return SBSE_OK;
+}
 }  // namespace sbse
 
 
@@ -1323,6 +1329,54 @@ int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int
     for (int k = 0; k < n_pairs; ++k)
       CK(cudaMemcpy(w_out + (long long)k * ctx->ng, ctx->W + (long long)slots[k] * ctx->ng,
                     ctx->ng * sizeof(double), cudaMemcpyDeviceToHost));
+  return SBSE_OK;
+}
+
+int sbse_bare_W(sbse_ctx *ctx, int n_pairs, const int *pi, const int *pj) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  if (!pi || !pj || n_pairs < 1) return fail(ctx, SBSE_ERR_INVALID_ARG, "pairs missing");
+  const int P_all = ctx->n_o * (ctx->n_o + 1) / 2;
+  if (n_pairs > P_all) return fail(ctx, SBSE_ERR_INVALID_ARG, "more pairs than n_o(n_o+1)/2");
+  std::vector<int> slots(n_pairs);
+  std::vector<char> seen(P_all, 0);
+  for (int k = 0; k < n_pairs; ++k) {
+    if (pi[k] < 0 || pj[k] < pi[k] || pj[k] >= ctx->n_o)
+      return fail(ctx, SBSE_ERR_INVALID_ARG, "pair indices must satisfy 0 <= i <= j < n_o");
+    slots[k] = pair_index(ctx->n_o, pi[k], pj[k]);
+    if (seen[slots[k]]) return fail(ctx, SBSE_ERR_INVALID_ARG, "duplicate pair");
+    seen[slots[k]] = 1;
+  }
+  CK(cudaSetDevice(ctx->device));
+  const long long ng = ctx->ng;
+  const int S = (n_pairs + 1) / 2;
+  const int base = ctx->n_occ - ctx->n_o;
+  void *vp;
+  int rc;
+  if ((rc = ensure(ctx, WS_IDX, (size_t)S * sizeof(int4), &vp))) return rc;
+  int4 *prod = (int4 *)vp;
+  if ((rc = ensure(ctx, WS_PW, (size_t)S * ng * sizeof(C2<double>), &vp))) return rc;
+  C2<double> *pw = (C2<double> *)vp;
+  if ((rc = ensure(ctx, WS_WACC, (size_t)n_pairs * ng * sizeof(double), &vp))) return rc;
+  double *q = (double *)vp;
+  std::vector<int4> pr(S);
+  for (int s = 0; s < S; ++s) {
+    const int k0 = 2 * s, k1 = 2 * s + 1;
+    pr[s] = make_int4(base + pi[k0], base + pj[k0], k1 < n_pairs ? base + pi[k1] : -1,
+                      k1 < n_pairs ? base + pj[k1] : -1);
+  }
+  CK(cudaMemcpyAsync(prod, pr.data(), S * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  // q_ij = v (phi_i phi_j), FP64, the orbitals of the FP64 tables whatever the precision mode
+  if ((rc = poisson_products<double>(ctx, ctx->g64, ctx->phi64, prod, n_pairs, pw, nullptr, q))) return rc;
+  for (int k = 0; k < n_pairs; ++k) {
+    CK(cudaMemcpyAsync(ctx->W + (long long)slots[k] * ng, q + (long long)k * ng, ng * sizeof(double),
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->have[slots[k]] = 1;
+  }
+  ctx->dab_given = false;
+  ctx->have_A = false;
+  CK(cudaStreamSynchronize(ctx->stream));
   return SBSE_OK;
 }
 

@@ -667,8 +667,9 @@ const double *launch_clean(const GridTables<T> &g, const T *phi_occ, int n_occ, 
   double *npart = ov + (long long)n_cols * n_occ * 2;
   double *sums = npart + ptb * n_cols * 2;
   double *cm1 = sums + (long long)n_cols * 2;
-  if (phi_ov && sizeof(T) == sizeof(float)) {
-    launch_umma_clean_ov(reinterpret_cast<const float *>(d), n_cols, phi_ov, n_occ, g.ng, dV, ov, part, err, s);
+  if (phi_ov && sizeof(T) == sizeof(float) &&
+      launch_umma_clean_ov(reinterpret_cast<const float *>(d), n_cols, phi_ov, n_occ, g.ng, dV, ov, part, err,
+                           s) == 0) {
   } else if (use_tc && sizeof(T) == sizeof(float)) {
     launch_umma_clean_overlap(reinterpret_cast<const float *>(d), n_cols,
                               reinterpret_cast<const float *>(phi_occ), n_occ, g.ng, dV, ov, part, err, s);

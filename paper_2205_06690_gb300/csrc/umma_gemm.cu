@@ -11,8 +11,11 @@
 // without swizzle (8-row x 16-byte core matrices: K-adjacent core matrices 128 B apart, row groups
 // 1024 B apart). Thread 0 issues the MMAs and commits them to one mbarrier per stage; every wait on
 // an mbarrier is bounded and sets *err on timeout. Partials (FP64) are reduced by the caller.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "kernels.h"
 #include "tma.cuh"
@@ -616,8 +619,9 @@ int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const floa
 // index. One CTA owns 64 complex columns of d (128 accumulator rows: real and imaginary part of each
 // column) times every occupied state (up to 512 accumulator columns in tensor memory), over a chunk
 // of grid points. Warp roles:
-//   warp 4     bulk copies: the raw interleaved FP32 d rows of a 32-point stage (one copy per
-//              column) and the stage's slab of pre-split phi tiles (one copy), on one mbarrier;
+//   warp 4     bulk copies: the raw interleaved FP32 d rows of a 32-point stage (two tiled
+//              tensor copies of 64 rows x 128 B, 128-byte swizzle, zero fill outside d) and the
+//              stage's slab of pre-split phi tiles (one copy), on one mbarrier;
 //   warps 0-3  split the raw stage into BF16 hi / lo rows 2c, 2c + 1 of the A tile (shared memory
 //              to shared memory), then, after the last stage, read the accumulator (one TMEM lane
 //              quarter each) and write the FP64 partials of the chunk;
@@ -628,12 +632,13 @@ int launch_umma_clean_overlap(const float *d_interleaved, int n_cols, const floa
 // and *err, and the copies and MMAs already issued are waited for before memory is released.
 constexpr int kOvKS = 32;                           // grid points per stage
 constexpr int kOvCols = kUmM / 2;                   // complex columns of d per CTA
-constexpr int kOvRawLd = kOvKS * 8 + 16;            // bytes per raw column in shared memory (padded)
-constexpr unsigned kOvRaw = kOvCols * kOvRawLd;     // 17408
+constexpr unsigned kOvRawHalf = kOvCols * 128;      // one tensor-copy box: 64 rows x 16 points
+constexpr unsigned kOvRaw = 2 * kOvRawHalf;         // 16384 (1024-byte aligned: the swizzle atom)
 constexpr unsigned kOvA = 2u * kUmM * kOvKS * 2;    // hi + lo A tile: 16384
 constexpr int kOvThreads = 192;
 constexpr int kOvMaxStages = 8;
 constexpr size_t kOvSmemBudget = 200u * 1024u;
+constexpr unsigned kOvAlign = 1024;                 // dynamic shared memory is aligned up to this
 
 __host__ __device__ constexpr unsigned ov_b_bytes(int nb) { return 2u * (unsigned)nb * kOvKS * 2; }
 __host__ __device__ constexpr unsigned ov_stage_bytes(int nb) { return kOvRaw + kOvA + ov_b_bytes(nb); }
@@ -696,10 +701,22 @@ __device__ __forceinline__ void ov_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// byte offset of the 16-byte chunk j of row r in a 128-byte-swizzled box of 128-byte rows
+__device__ __forceinline__ uint32_t swz128(int r, int j) { return (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)(uintptr_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __global__ void __launch_bounds__(kOvThreads, 1)
-    k_umma_clean_ov(const float2 *d, int n_cols, const uint8_t *phi_t, int nb, int n_occ, long long ng,
-                    long long kchunk, int S, double *part, int *err) {
-  extern __shared__ __align__(128) uint8_t smem[];
+    k_umma_clean_ov(const __grid_constant__ CUtensorMap dmap, int n_cols, const uint8_t *phi_t, int nb, int n_occ,
+                    long long ng, long long kchunk, int S, double *part, int *err) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *smem = smem_raw + ((kOvAlign - (smem_u32(smem_raw) & (kOvAlign - 1))) & (kOvAlign - 1));
   __shared__ __align__(8) uint64_t full[kOvMaxStages], conv[kOvMaxStages], empty[kOvMaxStages], accb;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -750,12 +767,15 @@ __global__ void __launch_bounds__(kOvThreads, 1)
         break;
       }
       const long long k0 = kbeg + (long long)it * kOvKS;
-      const int npts = (int)min((long long)kOvKS, kend - k0);  // even: ng and k0 are
-      if (lane == 0) tma_bar_expect(&full[s], (unsigned)ncols_t * npts * 8u + bbytes);
+      if (lane == 0) {
+        // d viewed as n_cols rows of 2 ng floats: boxes of 64 rows x 32 floats at float x = 2 k0
+        // (+ 32), a multiple of 64 (16-byte rule); rows past n_cols and points past ng read as zero
+        tma_bar_expect(&full[s], kOvRaw + bbytes);
+        tma_load_2d(raw + (size_t)s * kOvRaw, &dmap, (int)(2 * k0), c0, &full[s]);
+        tma_load_2d(raw + (size_t)s * kOvRaw + kOvRawHalf, &dmap, (int)(2 * k0 + 32), c0, &full[s]);
+        tma_load_1d(btile + (size_t)s * bbytes, phi_t + (size_t)(k0 / kOvKS) * bbytes, bbytes, &full[s]);
+      }
       __syncwarp();
-      for (int c = lane; c < ncols_t; c += 32)
-        tma_load_1d(raw + (size_t)s * kOvRaw + c * kOvRawLd, d + (long long)(c0 + c) * ng + k0, npts * 8u, &full[s]);
-      if (lane == 0) tma_load_1d(btile + (size_t)s * bbytes, phi_t + (size_t)(k0 / kOvKS) * bbytes, bbytes, &full[s]);
       ++issued;
     }
   } else if (warp == 5) {
@@ -806,24 +826,20 @@ __global__ void __launch_bounds__(kOvThreads, 1)
       uint8_t *ahi = atile + (size_t)s * kOvA, *alo = ahi + kUmM * kOvKS * 2;
 #pragma unroll
       for (int pass = 0; pass < 2; ++pass) {
+        // points 8g .. 8g + 7 of column col: box g / 2, 16-byte chunks 4 (g % 2) + q of row col
+        // (consecutive lanes take consecutive rows, whose swizzled chunks fall in distinct banks)
         const int col = t & (kOvCols - 1), g = (t >> 6) + 2 * pass;
+        const uint8_t *box = rs + (g >> 1) * kOvRawHalf;
         float re[8], im[8];
-        if (col < ncols_t && g * 8 + 8 <= npts) {
-          const float4 *src = reinterpret_cast<const float4 *>(rs + col * kOvRawLd + g * 64);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 v = src[q];
-            re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
-          }
-        } else {
-          const float2 *src = reinterpret_cast<const float2 *>(rs + col * kOvRawLd + g * 64);
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = *reinterpret_cast<const float4 *>(box + swz128(col, 4 * (g & 1) + q));
+          re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
+        }
+        if (g * 8 + 8 > npts) {  // the chunk ends inside this stage: points past it belong to no one here
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const bool in = col < ncols_t && g * 8 + j < npts;
-            const float2 v = in ? src[j] : make_float2(0.f, 0.f);
-            re[j] = v.x;
-            im[j] = v.y;
-          }
+          for (int j = 0; j < 8; ++j)
+            if (g * 8 + j >= npts) re[j] = im[j] = 0.f;
         }
         uint4 hi, lo;
         split8(re, &hi, &lo);
@@ -891,13 +907,31 @@ static void ov_grid(int n_cols, long long ng, int *m_tiles, long long *kc, long 
 }
 
 static int ov_stages(int nb) {
-  int s = (int)(kOvSmemBudget / ov_stage_bytes(nb));
+  int s = (int)((kOvSmemBudget - kOvAlign) / ov_stage_bytes(nb));
   return s > kOvMaxStages ? kOvMaxStages : s;
+}
+
+// the driver's tensor-map encoder, looked up once through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
 }
 
 bool umma_clean_ov_supported(int n_occ, long long ng) {
   const int nb = ov_rows(n_occ);
-  return nb <= 512 && (ng % 2) == 0 && ov_stages(nb) >= 2;
+  // rows of 2 ng floats: a 16-byte multiple stride; 2 ng < 2^32 for the tensor-copy coordinates
+  return nb <= 512 && (ng % 2) == 0 && 2 * ng < (1ll << 31) && ov_stages(nb) >= 2 && encode_tiled() != nullptr;
 }
 
 size_t umma_clean_ov_work_bytes(int n_cols, int n_occ, long long ng) {
@@ -914,11 +948,21 @@ int launch_umma_clean_ov(const float *d_interleaved, int n_cols, const uint8_t *
   int mt;
   long long kc, chunks;
   ov_grid(n_cols, ng, &mt, &kc, &chunks);
-  const size_t smem = (size_t)S * ov_stage_bytes(nb);
+  const size_t smem = (size_t)S * ov_stage_bytes(nb) + kOvAlign;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return -1;
+  CUtensorMap dmap;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ng), (cuuint64_t)n_cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * ng * sizeof(float))};
+  const cuuint32_t box[2] = {32u, (cuuint32_t)kOvCols};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (enc(&dmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d_interleaved, dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return -1;
   raise_smem_limit((const void *)k_umma_clean_ov, smem);
   dim3 grid((unsigned)mt, (unsigned)chunks);
-  k_umma_clean_ov<<<grid, kOvThreads, smem, s>>>(reinterpret_cast<const float2 *>(d_interleaved), n_cols, phi_t,
-                                                 nb, n_occ, ng, kc, S, work, err);
+  k_umma_clean_ov<<<grid, kOvThreads, smem, s>>>(dmap, n_cols, phi_t, nb, n_occ, ng, kc, S, work, err);
   count_launch(1);
   launch_reduce_cols(work, (int)chunks, 2 * n_cols * n_occ, scale, out, s);
   return 0;

@@ -11,6 +11,7 @@ from .model_system import (  # noqa: F401
     PRESETS,
     batch_presets,
     box_sweep_presets,
+    fno_presets,
     dense_eigensystem,
     gaussian_wells,
     local_potential,

@@ -91,6 +91,18 @@ def batch_presets(first_seed: int = 100, count: int = 64):
     return out
 
 
+def fno_presets(count: int, first_seed: int = 1000, N: int = 64, box: float = 24.0, n_steps: int = 2000):
+    """Training / evaluation systems of the learned form: 20 to 80 wells (drawn per seed), grid N^3
+    over a box of the paper-scale system's edge (so its fields resample onto this grid),
+    N_occ = round(1.5 n_wells), n_o = 8, n_c = 8, the paper-scale TDH parameters."""
+    out = []
+    for s in range(first_seed, first_seed + count):
+        n_wells = int(np.random.default_rng(s).integers(20, 81))
+        out.append(Preset(f"fno{s}", N=N, box=box, n_wells=n_wells, seed=s, n_occ=int(round(1.5 * n_wells)),
+                          n_o=8, n_c=8, n_steps=n_steps, gamma=0.1, n_exc=10))
+    return out
+
+
 def box_sweep_presets(base: Preset, boxes, n_steps: int | None = None):
     """The molecule of `base` (its wells, drawn for base.box) centred in boxes of the given edges at
     the same grid spacing (N = box / h): the runs of the finite-box correction of Sec. III."""
@@ -272,6 +284,6 @@ def dense_eigensystem(p: Preset):
     return v, e, (vec.T / np.sqrt(dV)).reshape(-1, p.N, p.N, p.N)
 
 
-__all__ = ["Preset", "PRESETS", "ModelSystem", "preset", "batch_presets", "box_sweep_presets",
+__all__ = ["Preset", "PRESETS", "ModelSystem", "preset", "batch_presets", "box_sweep_presets", "fno_presets",
            "preset_wells", "gaussian_wells",
            "local_potential", "make_system", "dense_eigensystem"]

@@ -161,3 +161,131 @@ def test_surrogate_trained_on_tdh_pairs_and_spot_checked():
     assert losses[-1] < 0.5 * losses[0]
     assert e1 < e0
     assert rep["surrogate_s_per_pair"] < rep["tdh_s_per_pair"]
+
+
+def _trilinear(src, nd):
+    """Periodic trilinear resampling of fields [..., n, n, n] onto nd^3 (test-side reference)."""
+    ns = src.shape[-1]
+    pos = np.arange(nd) * ns / nd
+    i0 = np.floor(pos).astype(int)
+    w = pos - i0
+    i1 = (i0 + 1) % ns
+    out = 0.0
+    for bz in (0, 1):
+        for by in (0, 1):
+            for bx in (0, 1):
+                iz, iy, ix = (i1 if bz else i0), (i1 if by else i0), (i1 if bx else i0)
+                wz, wy, wx = (w if bz else 1 - w), (w if by else 1 - w), (w if bx else 1 - w)
+                f = src[..., iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+                out = out + f * (wz[:, None, None] * wy[None, :, None] * wx[None, None, :])
+    return out
+
+
+def test_bare_potentials_add_and_resample():
+    """sbse_bare_W stores q_ij = v(phi_i phi_j) (the oracle's periodic Coulomb operator, 1e-10);
+    sbse_add_W adds scale * y to it; sbse_resample matches periodic trilinear interpolation (both
+    directions, 16^3 <-> 24^3, FP32)."""
+    torch = pytest.importorskip("torch")
+    import sbse_inputs as si
+    from oracle import tdh as otdh
+    from paper_2205_06690_gb300 import binding as Bd
+    p = si.preset("tiny16")
+    s = si.make_system(p)
+    N = p.N
+    g = otdh.Grid(N, p.box)
+    pairs = [(0, 0), (0, 1), (1, 1)]
+    base = p.n_occ - p.n_o
+    with Bd.Context(0, Bd.SBSE_MIXED) as c:
+        c.set_grid(N, p.box, s.v_loc)
+        c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi, s.eps, 0.5)
+        Bd.sbse_bare_W(c.h, pairs)
+        q = Bd.sbse_get_W(c.h, pairs, N ** 3)
+        for k, (i, j) in enumerate(pairs):
+            ref = otdh.coulomb_periodic(s.phi[base + i] * s.phi[base + j], g).ravel()
+            assert rel_err(q[k], ref) < 1e-10
+        rng = np.random.default_rng(5)
+        y = rng.standard_normal((len(pairs), N ** 3)).astype(np.float32)
+        yd = torch.from_numpy(y).cuda()
+        Bd.sbse_add_W(c.h, pairs, yd.data_ptr(), 0.25)
+        w = Bd.sbse_get_W(c.h, pairs, N ** 3)
+        assert np.max(np.abs(w - (q + 0.25 * y.astype(np.float64)))) < 1e-12
+        f = rng.standard_normal((3, N, N, N)).astype(np.float32)
+        for n_dst in (24, 16, 12):
+            src = torch.from_numpy(f).cuda()
+            dst = torch.empty((3, n_dst, n_dst, n_dst), dtype=torch.float32, device="cuda")
+            Bd.sbse_resample(c.h, 3, N, src.data_ptr(), n_dst, dst.data_ptr())
+            assert rel_err(dst.cpu().numpy(), _trilinear(f.astype(np.float64), n_dst)) < 1e-6
+        g24 = rng.standard_normal((2, 24, 24, 24)).astype(np.float32)
+        src = torch.from_numpy(g24).cuda()
+        dst = torch.empty((2, N, N, N), dtype=torch.float32, device="cuda")
+        Bd.sbse_resample(c.h, 2, 24, src.data_ptr(), N, dst.data_ptr())
+        assert rel_err(dst.cpu().numpy(), _trilinear(g24.astype(np.float64), N)) < 1e-6
+
+
+def test_polarisation_surrogate_on_a_coarser_network_grid():
+    """The polarisation form end to end on 24^3 systems with a 16^3 network: targets W - q from
+    TDH resampled to the network grid, training lowers the held-out error of W^pol, and the
+    surrogate-assisted W of a held-out system is q + the resampled prediction, with the spot pairs
+    carrying the propagated W."""
+    torch = pytest.importorskip("torch")
+    import sbse_inputs as si
+    from paper_2205_06690_gb300 import binding as Bd
+    from paper_2205_06690_gb300 import surrogate as S
+    N, NN, box = 24, 16, 12.0
+    prm = Bd.TDHParams(n_s=10, n_steps=60, clean_every=10, dt=0.05, gamma=0.1, alpha=1e-4, seed=3)
+    systems = []
+    for seed in range(1100, 1105):
+        p = si.model_system.Preset(f"s{seed}", N=N, box=box, n_wells=6, seed=seed, n_occ=9, n_o=4, n_c=2)
+        systems.append((p, si.make_system(p)))
+    one = S.Scales(1.0, 1.0, 1.0)
+    xs, ts = [], []
+    for p, s in systems[:4]:
+        with Bd.Context(0, Bd.SBSE_MIXED) as c:
+            c.set_grid(N, box, s.v_loc)
+            c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi, s.eps, 0.5)
+            pairs = [(i, j) for i in range(p.n_o) for j in range(i, p.n_o)]
+            xs.append(S.net_inputs(c, pairs, N, NN, one))
+            ts.append(S.polarisation_targets(c, prm, pairs, N, NN))
+            assert ts[-1].shape == (len(pairs), NN ** 3)
+    x = torch.cat(xs)
+    t = torch.cat(ts)
+    sc = S.Scales(float(x[:, 0].std()), float(x[:, 1].std()), float(t.std()))
+    x[:, 0] /= sc.s_rho
+    x[:, 1] /= sc.s_v
+    t /= sc.s_w
+    net = Bd.FNO(NN, width=12, modes=4, layers=4, max_batch=4)
+    S.init_params(net, seed=1)
+    p, s = systems[4]
+    pairs = [(i, j) for i in range(p.n_o) for j in range(i, p.n_o)]
+    with Bd.Context(0, Bd.SBSE_MIXED) as c:
+        c.set_grid(N, box, s.v_loc)
+        c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi, s.eps, 0.5)
+        pol_ref = S.polarisation_targets(c, prm, pairs, N, N).cpu().numpy().astype(np.float64)
+        xh = S.net_inputs(c, pairs, N, NN, sc)
+
+        def held_out_err():
+            y = torch.empty((len(pairs), NN ** 3), dtype=torch.float32, device="cuda")
+            for k0 in range(0, len(pairs), 4):
+                nb = min(4, len(pairs) - k0)
+                net.forward(nb, xh[k0:k0 + nb].data_ptr(), y[k0:k0 + nb].data_ptr())
+            yr = torch.empty((len(pairs), N ** 3), dtype=torch.float32, device="cuda")
+            Bd.sbse_resample(c.h, len(pairs), NN, y.data_ptr(), N, yr.data_ptr())
+            pol = sc.s_w * yr.cpu().numpy().astype(np.float64)
+            return float(np.linalg.norm(pol - pol_ref) / np.linalg.norm(pol_ref)), pol
+
+        e0, _ = held_out_err()
+        hist = S.train_schedule(net, x, t, epochs=40, batch=4, lr0=3e-3, lr1=1e-4)
+        e1, pol = held_out_err()
+        Bd.sbse_bare_W(c.h, pairs)
+        q = Bd.sbse_get_W(c.h, pairs, N ** 3)
+        rep = S.surrogate_pol_apply_W(c, net, sc, prm, pairs, N, spot_frac=0.2, tol=10.0, seed=2)
+        w = Bd.sbse_get_W(c.h, pairs, N ** 3)
+        spot = set(rep["spot_pairs"])
+        for k, pr in enumerate(pairs):
+            if pr in spot:  # the propagated W (same seed and parameters as pol_ref)
+                assert rel_err(w[k] - q[k], pol_ref[k]) < 1e-3
+            else:  # q + the resampled prediction
+                assert rel_err(w[k] - q[k], pol[k]) < 1e-5
+        assert not rep["fallback"]
+    assert hist[-1] < 0.5 * hist[0]
+    assert e1 < e0
