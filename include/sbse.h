@@ -369,6 +369,39 @@ int sbse_fno_pair_inputs(sbse_ctx *ctx, int n_pairs, const int *pi, const int *p
 int sbse_surrogate_W(sbse_ctx *ctx, sbse_fno *fno, int n_pairs, const int *pi, const int *pj, double s_rho,
                      double s_v, double s_w);
 
+/* Debug bounds checks (race detection and sanitizers are not available on the target; see the
+ * debug build, SBSE_DEBUG_BOUNDS=1 in paper_2205_06690_gb300/build.py, libsbse_dbg.so). In that
+ * build the kernels of the hot path check their global-memory indices; an out-of-range access is
+ * recorded (first one per translation unit) and redirected to element 0 of its array instead of
+ * faulting. *enabled = 1 in the debug build, 0 otherwise; *first_fault = 0 if nothing was recorded
+ * since the last call, else (site << 40) | (index & (2^40 - 1)) of the first record, site =
+ * translation unit * 100000 + source line. Reading clears the records. Host-synchronous.
+ * Returns OK (no record), NUMERIC (records found), CUDA. */
+int sbse_debug_bounds(int *enabled, unsigned long long *first_fault);
+
+/* Checkpoint / resume of a propagation (not in the paper: long runs and restarts).
+ * sbse_apply_W_range runs the time steps [n_begin, n_end) of the propagation sbse_apply_W would run
+ * for these parameters and pairs (0 <= n_begin < n_end <= p->n_steps): n_begin = 0 starts it
+ * (stochastic orbitals of Eq. 14 and the kick); n_begin > 0 continues the state this context holds,
+ * which a range ending at n_begin with the same parameters and pairs left (or sbse_load_state
+ * loaded); n_end = p->n_steps ends it and stores the pairs' W as sbse_apply_W does (w_out as there;
+ * before that W is not touched and w_out is ignored). Calls in the same context between the range
+ * calls may discard the state (they share its device memory): a later continuation then returns
+ * NOT_READY. The continued run gives the same W as one sbse_apply_W call, to the bit in both
+ * precision modes (the partial FP32 time integral is part of the state).
+ * sbse_state_bytes / sbse_save_state copy the held state (the difference orbitals d, eta0 of the next
+ * step, the FP64 and partial FP32 time integrals, E - 1 of the pending half step, the orbitals'
+ * norms, and the parameters, pairs and next step) into a HOST buffer of at least that many bytes;
+ * sbse_load_state puts such a buffer into a context of the same grid, orbitals and precision (for
+ * example a new process) for the next sbse_apply_W_range call.
+ * Errors: INVALID_ARG (range, buffer), NOT_READY (no such state), SHAPE (other grid or precision),
+ * NUMERIC, OOM, CUDA, DEVICE_TIMEOUT. */
+int sbse_apply_W_range(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int *pi, const int *pj,
+                       const double *coeff, double *w_out, int n_begin, int n_end);
+int sbse_state_bytes(sbse_ctx *ctx, size_t *bytes);
+int sbse_save_state(sbse_ctx *ctx, void *host, size_t bytes);
+int sbse_load_state(sbse_ctx *ctx, const void *host, size_t bytes);
+
 /* Bare potentials q_ij = v (phi_i phi_j) (FP64 Poisson, the first term of W_ij = q_ij + W^pol_ij,
  * Sec. II.B) stored as the W of the given pairs of the valence window, as a starting point for a
  * polarisation part added by sbse_add_W. Errors: INVALID_ARG (indices, duplicates), NOT_READY, OOM,

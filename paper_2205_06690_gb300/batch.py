@@ -7,9 +7,9 @@ alone would not, and from the second run on every system's time loop is a graph 
 run of a batch goes one system at a time: under CUDA's lazy module loading the first launch of a
 kernel loads its module, which would invalidate another thread's graph capture in progress; after
 one run every kernel is loaded and every graph captured.
-`autotune` picks, per grid size, the fastest split-operator variant that the grid supports (three
-pass kernels or the persistent step kernel; plain or bulk-copy streamed passes) from a short timed
-trial, and caches the choice.
+`autotune` picks, per grid size and pair count, the fastest split-operator variant that the grid
+supports (three pass kernels or the persistent step kernel; plain or bulk-copy streamed passes;
+all pairs per pass or L2-sized chunks of pairs) from a short timed trial, and caches the choice.
 """
 from __future__ import annotations
 
@@ -39,12 +39,24 @@ class BatchItem:
     seed: int = 0  # stochastic coefficient seed of the system
 
 
-def _variants(n: int, precision: int):
-    """(persistent, tma_planes) pairs that change the kernels on this grid."""
+# pair-chunk sizes tried (SBSE_OPT_CHUNK_MB; 0 = every pair in one pass): one chunk near half of L2
+_CHUNKS_MB = (0, 64)
+
+
+def _variants(n: int, precision: int, pair_bytes: float):
+    """(persistent, tma_planes, chunk_mb) triples that change the kernels or their launches on this
+    grid; chunking is tried only where the pair batch does not fit in one chunk."""
+    chunks = [c for c in _CHUNKS_MB if c == 0 or pair_bytes > c * 2 ** 20]
     if n in (80, 96) and precision == B.SBSE_MIXED:
-        return [(0, 1)]  # the two-sweep passes: one variant
+        return [(0, 1, c) for c in chunks]  # the two-sweep passes
     tma = [0, 1] if (precision == B.SBSE_MIXED and n in (32, 40, 48, 64)) else [1]
-    return [(p, t) for p in (0, 1) for t in tma]
+    out = []
+    for p in (0, 1):
+        for t in tma:
+            for c in chunks:
+                if p == 0 or c == 0:  # the persistent kernel takes every pair at once
+                    out.append((p, t, c))
+    return out
 
 
 def autotune(ctx: B.Context, item: BatchItem, params: B.TDHParams, trial_steps: int = 6) -> dict:
@@ -53,20 +65,26 @@ def autotune(ctx: B.Context, item: BatchItem, params: B.TDHParams, trial_steps: 
     if key not in _TUNED:
         trial = dataclasses.replace(params, n_steps=trial_steps, clean_every=0)
         pairs = [(i, j) for i in range(item.n_o) for j in range(i, item.n_o)]
+        pair_bytes = len(pairs) * params.n_s * item.n ** 3 * (8 if ctx.precision == B.SBSE_MIXED else 16)
         best = None
-        for persistent, tma in _variants(item.n, ctx.precision):
-            B.sbse_set_option(ctx.h, B.SBSE_OPT_PERSISTENT, persistent)
-            B.sbse_set_option(ctx.h, B.SBSE_OPT_TMA_PLANES, tma)
+        for persistent, tma, chunk in _variants(item.n, ctx.precision, pair_bytes):
+            _set(ctx, persistent, tma, chunk)
             ctx.apply_W(trial, pairs)  # warm-up of this variant
             t0 = time.perf_counter()
             ctx.apply_W(trial, pairs)
             dt = time.perf_counter() - t0
-            if best is None or dt < best[2]:
-                best = (persistent, tma, dt)
-        _TUNED[key] = {"persistent": best[0], "tma_planes": best[1], "trial_s": best[2]}
-    B.sbse_set_option(ctx.h, B.SBSE_OPT_PERSISTENT, _TUNED[key]["persistent"])
-    B.sbse_set_option(ctx.h, B.SBSE_OPT_TMA_PLANES, _TUNED[key]["tma_planes"])
-    return _TUNED[key]
+            if best is None or dt < best[3]:
+                best = (persistent, tma, chunk, dt)
+        _TUNED[key] = {"persistent": best[0], "tma_planes": best[1], "chunk_mb": best[2], "trial_s": best[3]}
+    t = _TUNED[key]
+    _set(ctx, t["persistent"], t["tma_planes"], t["chunk_mb"])
+    return t
+
+
+def _set(ctx, persistent: int, tma: int, chunk_mb: int):
+    B.sbse_set_option(ctx.h, B.SBSE_OPT_PERSISTENT, persistent)
+    B.sbse_set_option(ctx.h, B.SBSE_OPT_TMA_PLANES, tma)
+    B.sbse_set_option(ctx.h, B.SBSE_OPT_CHUNK_MB, chunk_mb)
 
 
 class Batch:

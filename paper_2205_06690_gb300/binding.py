@@ -14,7 +14,8 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsbse.so")
+# SBSE_DEBUG_BOUNDS=1 loads the debug build (device-side index checks, see sbse_debug_bounds)
+LIB_PATH = os.path.join(_HERE, "libsbse_dbg.so" if os.environ.get("SBSE_DEBUG_BOUNDS") == "1" else "libsbse.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "sbse.h")
 
 SBSE_OK = 0
@@ -131,6 +132,11 @@ def load() -> C.CDLL:
         "sbse_fno_pair_inputs": (i, [vp, i, ip, ip, d, d, vp]),
         "sbse_surrogate_W": (i, [vp, vp, i, ip, ip, d, d, d]),
         "sbse_bare_W": (i, [vp, i, ip, ip]),
+        "sbse_apply_W_range": (i, [vp, C.POINTER(sbse_tdh_params), i, ip, ip, dp, dp, i, i]),
+        "sbse_debug_bounds": (i, [C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)]),
+        "sbse_state_bytes": (i, [vp, C.POINTER(C.c_size_t)]),
+        "sbse_save_state": (i, [vp, vp, C.c_size_t]),
+        "sbse_load_state": (i, [vp, vp, C.c_size_t]),
         "sbse_add_W": (i, [vp, i, ip, ip, vp, d]),
         "sbse_resample": (i, [vp, i, i, vp, i, vp]),
     })
@@ -245,6 +251,43 @@ def sbse_fno_pair_inputs(ctx, pairs, s_rho: float, s_v: float, x_ptr: int) -> No
 def sbse_surrogate_W(ctx, fno_handle, pairs, s_rho: float, s_v: float, s_w: float) -> None:
     pi, pj, a, b = _pairs_c(pairs)
     _check(ctx, load().sbse_surrogate_W(ctx, fno_handle, len(pairs), a, b, s_rho, s_v, s_w))
+
+
+def sbse_apply_W_range(ctx, params: TDHParams, pairs, n_begin: int, n_end: int, coeff=None,
+                       n_g: int | None = None):
+    """Time steps [n_begin, n_end) of the propagation of `pairs` (checkpoint / resume); returns W
+    when n_end == params.n_steps and n_g is given."""
+    pi, pj, a, b = _pairs_c(pairs)
+    cf = None if coeff is None else _f64(coeff)
+    out = None if (n_g is None or n_end < params.n_steps) else np.empty((len(pairs), n_g))
+    cp = params.to_c()
+    _check(ctx, load().sbse_apply_W_range(ctx, C.byref(cp), len(pairs), a, b, _dptr(cf), _dptr(out),
+                                          n_begin, n_end))
+    return out
+
+
+def sbse_debug_bounds():
+    """(enabled, first_fault): whether this is the debug build, and the first out-of-range index
+    recorded since the last call (0: none); reading clears the records."""
+    en, f = C.c_int(), C.c_ulonglong()
+    rc = load().sbse_debug_bounds(C.byref(en), C.byref(f))
+    if rc not in (SBSE_OK, SBSE_ERR_NUMERIC):
+        _check(None, rc)
+    return bool(en.value), int(f.value)
+
+
+def sbse_save_state(ctx) -> np.ndarray:
+    """The propagation state held by the context, as a host byte array."""
+    n = C.c_size_t()
+    _check(ctx, load().sbse_state_bytes(ctx, C.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(ctx, load().sbse_save_state(ctx, buf.ctypes.data_as(C.c_void_p), n.value))
+    return buf
+
+
+def sbse_load_state(ctx, buf: np.ndarray) -> None:
+    a = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(ctx, load().sbse_load_state(ctx, a.ctypes.data_as(C.c_void_p), a.size))
 
 
 def sbse_bare_W(ctx, pairs) -> None:

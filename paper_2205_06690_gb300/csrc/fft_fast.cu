@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "fft_reg.cuh"
+#include "bounds.cuh"
 #include "kernels.h"
 #include "passes.cuh"
 #include "tma.cuh"
@@ -185,6 +186,8 @@ __global__ void __launch_bounds__(fwd_ppb<T, N, PAIR>() * N)
   // PPB divides N: the block's planes z0 .. z0 + PPB - 1 are contiguous inside one item
   const long long p0 = (long long)blockIdx.x * PPB;
   const long long item = p0 / N;
+  (void)SBSE_IDX(p0 + PPB - 1, planes_total);
+  (void)SBSE_IDX(item, a.n_items);
   fwd_planes<T, N, PAIR, PPB>(g, a, item, (p0 - item * N) * NN, reinterpret_cast<C2<T> *>(smem_raw));
 }
 
@@ -280,6 +283,7 @@ __device__ __forceinline__ void inv_density_planes(const GView<T> &g, C2<T> *dat
   for (int k = 0; k < N; ++k) accd[k] = T(0);
   for (int ell = 0; ell < L; ++ell) {
     const long long item = (long long)pair * L + ell;
+    (void)SBSE_IDX((long long)z0 * NN + NN * PPB - 1, g.ng);  // the block's planes inside the item
     C *base = data + item * g.ng + (long long)z0 * NN;
     plane_inverse<T, N, COH>(S, base, pl, q);
     const C *ab = a_next + (long long)ell * g.ng + (long long)z0 * NN;

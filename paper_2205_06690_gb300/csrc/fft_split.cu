@@ -30,7 +30,9 @@
 
 #include "fft_reg.cuh"
 #include "kernels.h"
+#include "bounds.cuh"
 #include "passes.cuh"
+#include "tma.cuh"
 
 namespace sbse {
 
@@ -126,6 +128,9 @@ __device__ __forceinline__ void preop_plane(const GView<float> &g, const XfwdArg
   using C = float2;
   constexpr int LD = N + 1, NT = 2 * N, KP = N / 2, UB = 8;
   const PreopItem<float> it = preop_item<float>(g, a, item);
+  (void)SBSE_IDX(item, a.n_items);
+  (void)SBSE_IDX(off + threadIdx.x + (long long)(KP - 1) * NT, g.ng);  // the largest point this thread reads
+  if constexpr (PAIR) (void)SBSE_IDX(item / a.L, a.n_items / a.L);     // the pair of E - 1
   const int y0 = threadIdx.x / N;
   C *srow = S + y0 * LD + (threadIdx.x - y0 * N);
   if constexpr (PAIR) {
@@ -216,6 +221,7 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_fwd2(GView<flo
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = col[(2 * m + s) * LD];
     fft2_dit<N, -1>(v, s);
+    (void)SBSE_IDX(off + p + (long long)(N - 1) * N, g.ng);
     C *out = a.out + item * g.ng + off + p;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -263,6 +269,7 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_kin2(GView<flo
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = col[(2 * m + s) * LD];
     kin_roundtrip<N>(v, s, tab);
+    (void)SBSE_IDX(off + p + (long long)(N - 1) * N, g.ng);
     C *out = a.out + item * g.ng + off + p;
 #pragma unroll
     for (int m = 0; m < H; ++m) out[(2 * m + s) * N] = v[m];
@@ -288,8 +295,10 @@ __global__ void __launch_bounds__(128, 3) k_zkin2(GView<float> g, float2 *data, 
   const int lane = threadIdx.x & 31, s = lane >> 4, cw = (threadIdx.x >> 5) * 16 + (lane & 15);
   const int rem = cs * 64 + cw;
   const int n_orb = DENS ? L : 1;
+  (void)SBSE_IDX(rem, NN);
   for (int ell = 0; ell < n_orb; ++ell) {
     const long long item = DENS ? (long long)unit * L + ell : unit;
+    (void)SBSE_IDX(item, (long long)n_units * n_orb);
     C *base = data + item * g.ng + rem;
     C v[H];
 #pragma unroll
@@ -326,17 +335,124 @@ __global__ void __launch_bounds__(128, 3) k_zkin2(GView<float> g, float2 *data, 
   }
 }
 
+// The same sweep for the pair batch with the columns of the next orbital staged in shared memory
+// by one bulk tensor copy (N z-rows x ZT_CW columns) while the current orbital is transformed, so
+// the column loads no longer stall the warps. ZT_CW = 32 columns (two warps) per block keep the
+// stage (24 KB at N = 96) and the density rows small enough for five blocks per SM.
+constexpr int kZtCw = 32;
+constexpr int kZtPitch = kZtCw + 16;  // density rows: the two half-warps' rows fall on different banks
+
+// dynamic shared memory of the staged z sweep: the stage and the density rows, plus the slack that
+// lets the kernel start the stage on a 128-byte boundary (the alignment a tensor copy's shared
+// destination needs; the dynamic region itself follows the static variables)
+constexpr unsigned kZtAlign = 128;
+template <int N> constexpr size_t ztma_smem() {
+  return (size_t)N * kZtCw * sizeof(float2) + (size_t)N * kZtPitch * sizeof(float) + kZtAlign;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          tma_smem_addr(dst)),
+      "l"((uint64_t)(uintptr_t)map), "r"(x), "r"(y), "r"(z), "r"(tma_smem_addr(bar))
+      : "memory");
+}
+
+template <int N>
+__global__ void __launch_bounds__(2 * kZtCw, 5)
+    k_zkin2_tma(const __grid_constant__ CUtensorMap dmap, GView<float> g, float2 *data, const float2 *a_next,
+                float *dens, int n_units, int L, int *err) {
+  using C = float2;
+  constexpr int NN = N * N, H = N / 2, UB = 16;
+  constexpr unsigned kStage = (unsigned)N * kZtCw * sizeof(C);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((kZtAlign - (tma_smem_addr(smem_raw) & (kZtAlign - 1))) & (kZtAlign - 1));
+  C *St = reinterpret_cast<C *>(smem);                    // [z][column], 128-byte aligned
+  float *D = reinterpret_cast<float *>(smem + kStage);    // [z][kZtPitch]
+  __shared__ C tab[3 * H];
+  __shared__ __align__(8) uint64_t bar;
+  const int cs = (int)(blockIdx.x / (unsigned)n_units);
+  const int unit = (int)blockIdx.x - cs * n_units;
+  const long long item0 = (long long)unit * L;
+  if (tma_smem_addr(St) & (kZtAlign - 1)) {  // never expected: report instead of issuing the copy
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    tma_bar_init(&bar, 1);
+    tma_bar_expect(&bar, kStage);
+    tma_load_3d(St, &dmap, 2 * cs * kZtCw, 0, (int)item0, &bar);
+  }
+  for (int i = threadIdx.x; i < 3 * H; i += blockDim.x) tab[i] = g.kin[N + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, s = lane >> 4, cw = (threadIdx.x >> 5) * 16 + (lane & 15);
+  const int rem = cs * kZtCw + cw;
+  (void)SBSE_IDX(rem, NN);
+  (void)SBSE_IDX(item0 + L - 1, (long long)n_units * L);
+  int failed = -1;  // the orbital whose copy did not land in time
+  for (int ell = 0; ell < L; ++ell) {
+    if (!__syncthreads_and(tma_bar_wait(&bar, (unsigned)(ell & 1)))) {
+      failed = ell;
+      break;
+    }
+    C v[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = St[(2 * m + s) * kZtCw + cw];
+    __syncthreads();  // every thread holds its columns: the stage can take the next orbital
+    if (threadIdx.x == 0 && ell + 1 < L) {
+      tma_fence_proxy();
+      tma_bar_expect(&bar, kStage);
+      tma_load_3d(St, &dmap, 2 * cs * kZtCw, 0, (int)(item0 + ell + 1), &bar);
+    }
+    kin_roundtrip<N>(v, s, tab);
+    C *base = data + (item0 + ell) * g.ng + rem;
+#pragma unroll
+    for (int m = 0; m < H; ++m) base[(long long)(2 * m + s) * NN] = v[m];
+    const C *ab = a_next + (long long)ell * g.ng + rem;
+#pragma unroll
+    for (int m0 = 0; m0 < H; m0 += UB) {
+      C a0[UB];
+#pragma unroll
+      for (int k = 0; k < UB; ++k)
+        if (m0 + k < H) a0[k] = ab[(long long)(2 * (m0 + k) + s) * NN];
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (m0 + k < H) {
+          const C dv = v[m0 + k];
+          const float t = 2.f * (2.f * (a0[k].x * dv.x + a0[k].y * dv.y) + dv.x * dv.x + dv.y * dv.y);
+          float &acc = D[(2 * (m0 + k) + s) * kZtPitch + cw];
+          acc = ell ? acc + t : t;
+        }
+      }
+      asm volatile("" ::: "memory");
+    }
+  }
+  if (failed >= 0) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 1);
+      tma_bar_wait(&bar, (unsigned)(failed & 1));  // the copy still in flight: a bounded chance to land
+    }
+    __syncthreads();
+    return;
+  }
+  __syncthreads();
+  float *db = dens + (long long)unit * g.ng + rem;
+#pragma unroll 8
+  for (int m = 0; m < H; ++m) db[(long long)(2 * m + s) * NN] = D[(2 * m + s) * kZtPitch + cw];
+}
+
 // ------------------------------------------------------------------------------------------
 // z columns: 64 columns per block of 128 threads (NN is a multiple of 64 for N = 80, 96)
 
 template <int N>
-__global__ void __launch_bounds__(128, 4) k_zcol2(GView<float> g, float2 *data, int mult) {
+__global__ void __launch_bounds__(128, 4) k_zcol2(GView<float> g, float2 *data, int mult, int n_items) {
   using C = float2;
   constexpr int NN = N * N, H = N / 2, Q = H / 2;
   const int lane = threadIdx.x & 31, s = lane >> 4;
   const long long c = (long long)blockIdx.x * 64 + (threadIdx.x >> 5) * 16 + (lane & 15);
   const long long item = c / NN;
   const int rem = (int)(c - item * NN), y = rem / N, x = rem - y * N;
+  (void)SBSE_IDX(item, n_items);
   C *base = data + item * g.ng + rem;
   C v[H];
 #pragma unroll
@@ -384,6 +500,8 @@ __global__ void __launch_bounds__(2 * N, N == 96 ? 2 : 3) k_plane_inv2(GView<flo
   const long long item = (long long)blockIdx.x - (long long)z * n_units;
   const long long off = (long long)z * NN;
   const int lane = threadIdx.x & 31, s = lane >> 4, p = (threadIdx.x >> 5) * 16 + (lane & 15);
+  (void)SBSE_IDX(off + p + (long long)(N - 1) * N, g.ng);
+  (void)SBSE_IDX(2 * item + 1, 2ll * n_units);  // the slot's two densities
   {  // y inverse FFTs from global (frequency blocks) into the tile (interleaved rows)
     C v[H];
     const C *col = data + item * g.ng + off + p;
@@ -470,13 +588,26 @@ template <int N> void kin2(const GridTables<float> &g, const XfwdArgs<float> &a,
 template <int N> void zcol2(const GridTables<float> &g, float2 *d, int n_items, int mult, cudaStream_t s) {
   static_assert((N * N) % 64 == 0, "z pass blocks hold 64 whole columns");
   const unsigned blocks = (unsigned)((long long)n_items * N * N / 64);
-  k_zcol2<N><<<blocks, 128, 0, s>>>(view(g), d, mult);
+  k_zcol2<N><<<blocks, 128, 0, s>>>(view(g), d, mult, n_items);
 }
 
 template <int N>
 void zkin2(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L, float *dens,
-           cudaStream_t s) {
+           cudaStream_t s, int *err) {
   const int units = dens ? n_items / L : n_items;
+  if (dens && err) {
+    // d as n_items orbitals x N z-planes x 2 N^2 floats; boxes of 2 ZT_CW floats x N planes x 1
+    CUtensorMap map;
+    const uint64_t dims[3] = {(uint64_t)2 * N * N, (uint64_t)N, (uint64_t)n_items};
+    const uint64_t strides[2] = {(uint64_t)N * N * sizeof(float2), (uint64_t)g.ng * sizeof(float2)};
+    const uint32_t box[3] = {2u * kZtCw, (uint32_t)N, 1u};
+    if (make_tensor_map_f32(&map, d, 3, dims, strides, box, false)) {
+      raise_smem_limit((const void *)k_zkin2_tma<N>, ztma_smem<N>());
+      const unsigned blocks = (unsigned)units * (N * N / kZtCw);
+      k_zkin2_tma<N><<<blocks, 2 * kZtCw, ztma_smem<N>(), s>>>(map, view(g), d, a_next, dens, units, L, err);
+      return;
+    }
+  }
   const unsigned blocks = (unsigned)units * (N * N / 64);
   if (dens)
     k_zkin2<N, true><<<blocks, 128, 0, s>>>(view(g), d, a_next, dens, units, L);
@@ -534,9 +665,9 @@ void launch_plane_kin2(const GridTables<float> &g, const XfwdArgs<float> &a, cud
 }
 
 void launch_zkin2(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L, float *dens,
-                  cudaStream_t s) {
-  if (g.N == 80) zkin2<80>(g, d, n_items, a_next, L, dens, s);
-  else if (g.N == 96) zkin2<96>(g, d, n_items, a_next, L, dens, s);
+                  cudaStream_t s, int *err) {
+  if (g.N == 80) zkin2<80>(g, d, n_items, a_next, L, dens, s, err);
+  else if (g.N == 96) zkin2<96>(g, d, n_items, a_next, L, dens, s, err);
 }
 
 }  // namespace sbse

@@ -1,6 +1,7 @@
 // Host-side interface between the translation units of the sbse library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,6 +14,11 @@ namespace sbse {
 void count_launch(int n);
 // raise (never lower) a kernel's dynamic shared memory limit to `bytes`, thread-safe
 void raise_smem_limit(const void *fn, size_t bytes);
+// tiled tensor map of an FP32 array for bulk tensor copies (dims / box innermost first, strides in
+// bytes of the rank - 1 outer dimensions; zero fill outside the array); false if the driver's
+// encoder is unavailable or rejects the layout
+bool make_tensor_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                         const uint64_t *strides_bytes, const uint32_t *box, bool swizzle128);
 
 // ---- register-pencil three-pass round trip (fft_fast.cu), for the sizes fast_supported<T>(N)
 int upload_reg_twiddles();
@@ -47,8 +53,10 @@ void launch_plane_inv2_poisson(const GridTables<float> &g, float2 *d, int n_slot
 // pre-operation + x and y kinetic operators; z kinetic operator + the pairs' induced density when
 // dens != null, L orbitals per pair)
 void launch_plane_kin2(const GridTables<float> &g, const XfwdArgs<float> &a, cudaStream_t s);
+// err != null: the pair batch's sweep (dens != null) stages each orbital's columns by bulk tensor
+// copies while the one before is transformed (bounded waits; *err set if one runs out)
 void launch_zkin2(const GridTables<float> &g, float2 *d, int n_items, const float2 *a_next, int L, float *dens,
-                  cudaStream_t s);
+                  cudaStream_t s, int *err = nullptr);
 // out = exp(-i V_loc tau), computed in FP64 from the FP64 potential v64
 template <typename T> void launch_phase_table(const double *v64, long long ng, double tau, C2<T> *out,
                                               cudaStream_t s);

@@ -26,6 +26,12 @@ void init_fft_kernels();
 void set_thread_error(const std::string &msg) { g_create_error = msg; }
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// readers of the debug bounds records, one per translation unit (debug build only)
+static std::vector<int (*)(unsigned long long *)> &bounds_readers() {
+  static std::vector<int (*)(unsigned long long *)> r;
+  return r;
+}
+void register_bounds_reader(int (*reader)(unsigned long long *)) { bounds_readers().push_back(reader); }
 // The dynamic shared memory limit is an attribute of the kernel, shared by every context and host
 // thread: lowering it for one launch could make another thread's larger launch of the same kernel
 // fail in between. So it is only ever raised, under a lock.
@@ -118,6 +124,14 @@ struct sbse_ctx {
   size_t held_bytes = 0, mem_limit = 0;
   // iteration limit of the persistent step kernel's waits on other tiles (SBSE_OPT_WAIT_LIMIT)
   unsigned wait_limit = 1u << 23;
+  // a propagation stopped part way (sbse_apply_W_range): its parameters, pairs and next step; the
+  // state itself is in the workspace (WS_D, WS_A0, WS_WACC, WS_ACC32, WS_EM1, WS_N0)
+  struct {
+    bool valid = false;
+    int next = 0;
+    sbse_tdh_params params{};
+    std::vector<int> slots;
+  } run;
 };
 
 namespace {
@@ -192,6 +206,9 @@ template <typename X> void dfree(sbse_ctx *ctx, X *&p) {
 int ensure(sbse_ctx *ctx, int slot, size_t bytes, void **out) {
   DevBuf &b = ctx->ws[slot];
   if (b.cap < bytes) {
+    // a stopped propagation keeps its state in these slots: growing one of them discards it
+    if (slot == WS_A0 || slot == WS_D || slot == WS_WACC || slot == WS_ACC32 || slot == WS_EM1 || slot == WS_N0)
+      ctx->run.valid = false;
     release(ctx, b.p);
     b.p = nullptr;
     b.cap = 0;
@@ -204,6 +221,7 @@ int ensure(sbse_ctx *ctx, int slot, size_t bytes, void **out) {
 }
 
 void free_scratch(sbse_ctx *ctx) {
+  ctx->run.valid = false;
   for (auto &b : ctx->ws) {
     release(ctx, b.p);
     b.p = nullptr;
@@ -401,7 +419,7 @@ void round_trip_orbitals(sbse_ctx *ctx, const GridTables<T> &g, const XfwdArgs<T
       }
       if (parts & RT_INV) {
         if (sub) clk_begin(ctx, 7, &ck);
-        launch_zkin2(g, data, n_items, a_next, L, dens, st);
+        launch_zkin2(g, data, n_items, a_next, L, dens, st, ctx->tma_planes ? ctx->flag : nullptr);
         count_launch(1);
         if (sub) clk_end(ctx, ck);
       }
@@ -485,9 +503,13 @@ int poisson_products(sbse_ctx *ctx, const GridTables<T> &g, const T *orb, const 
   return SBSE_OK;
 }
 
+// Runs the time steps [n_begin, n_end) of the propagation (0 and p->n_steps for a whole run).
+// n_begin > 0 continues from the state held in the workspace (d, eta0 of the step in WS_A0, the
+// time integral, E - 1, the norms), left by a range ending there or loaded by sbse_load_state;
+// n_end < n_steps leaves that state in the workspace instead of storing W.
 template <typename T>
 int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> &slots,
-                const std::vector<double> &coef_host) {
+                const std::vector<double> &coef_host, int n_begin, int n_end) {
   using C = C2<T>;
   GridTables<T> &g = tables<T>(ctx);
   const long long ng = ctx->ng;
@@ -526,13 +548,13 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   if (sizeof(T) != sizeof(double)) {
     if ((rc = ensure(ctx, WS_ACC32, (size_t)P * ng * sizeof(T), &vp))) return rc;
     accT = (T *)vp;
-    CK(cudaMemsetAsync(accT, 0, (size_t)P * ng * sizeof(T), st));
+    if (n_begin == 0) CK(cudaMemsetAsync(accT, 0, (size_t)P * ng * sizeof(T), st));
   }
   C *em1 = nullptr;
   if (p->feedback) {
     if ((rc = ensure(ctx, WS_EM1, (size_t)P * ng * sizeof(C), &vp))) return rc;
     em1 = (C *)vp;
-    CK(cudaMemsetAsync(em1, 0, (size_t)P * ng * sizeof(C), st));
+    if (n_begin == 0) CK(cudaMemsetAsync(em1, 0, (size_t)P * ng * sizeof(C), st));
   }
   if ((rc = ensure(ctx, WS_N0, (size_t)L * sizeof(double), &vp))) return rc;
   n0 = (double *)vp;
@@ -560,6 +582,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   prod = (int4 *)vp;
 
   CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), st));
+  if (n_begin == 0) {
   // ---- init: eta0_l (Eq. 14), N0_l, q_ij (FP64), kick
   CK(cudaMemcpyAsync(coef, coef_host.data(), coef_host.size() * sizeof(double),
                      cudaMemcpyHostToDevice, st));
@@ -588,6 +611,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     return rc;
   launch_kick<T>(g, wacc, P, a0, L, p->alpha, d, st);
   CHECK_LAUNCH("kick");
+  }
 
   // ---- time loop (Eq. 10 split-operator, Eq. 15 cleaning, Eq. 13 damped trapezoid)
   const int Nt = p->n_steps, M = p->clean_every;
@@ -662,7 +686,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
   };
   bool eta0_issued = false;  // the eta0 round trip of this step was issued during the last Poisson
   auto time_loop = [&]() -> int {
-  for (int n = 0; n < Nt; ++n) {
+  for (int n = n_begin; n < n_end; ++n) {
     bool pending = n > 0;
     const double *cm1_pending = nullptr;
     if (M > 0 && n % M == 0) {
@@ -730,7 +754,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     }
     CHECK_LAUNCH("step");
     clk_end(ctx, c0);
-    if (n + 1 < Nt && !(M > 0 && (n + 1) % M == 0)) {
+    if (n + 1 < n_end && !(M > 0 && (n + 1) % M == 0)) {
       // next step's eta0 round trip: reads this step's new eta0 (anext), overwrites acur, which
       // the pair batch above has finished reading; no cleaning in between, so its phase is full
       if ((rc = eta0_step(anext, acur, g.pv_dt))) return rc;
@@ -767,7 +791,7 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
       (unsigned long long)L, (unsigned long long)Nt, (unsigned long long)M, (unsigned long long)p->feedback,
       (unsigned long long)chunk_pairs, (unsigned long long)persistent, (unsigned long long)sizeof(T),
       (unsigned long long)(uintptr_t)sq.items, (unsigned long long)(uintptr_t)sq.claim,
-      (unsigned long long)sq.wait_limit};
+      (unsigned long long)sq.wait_limit, (unsigned long long)n_begin, (unsigned long long)n_end};
   for (double v : {p->dt, p->gamma, p->alpha, ctx->dV}) {
     unsigned long long b;
     memcpy(&b, &v, sizeof b);
@@ -823,6 +847,17 @@ int run_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, const std::vector<int> 
     CK(cudaStreamSynchronize(st));
     if (h) return fail(ctx, SBSE_ERR_DEVICE_TIMEOUT, "a bounded device-side wait timed out (persistent step or tensor-core cleaning)");
   }
+  if (n_end < Nt) {
+    // a range that stops early: the state stays in the workspace, with the current eta0 in WS_A0
+    // (every step swaps the two eta0 buffers)
+    if ((n_end - n_begin) % 2 == 1)
+      CK(cudaMemcpyAsync(a0, a1, (size_t)L * ng * sizeof(C), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->run.valid = true;
+    ctx->run.next = n_end;
+    return SBSE_OK;
+  }
+  ctx->run.valid = false;
   // results into the canonical slots
   for (int k = 0; k < P; ++k)
     CK(cudaMemcpyAsync(ctx->W + (long long)slots[k] * ng, wacc + (long long)k * ng,
@@ -1112,6 +1147,28 @@ void tridiag_extremes(const std::vector<double> &al, const std::vector<double> &
   *hi = kth(m - 1);
 }
 
+namespace {
+// layout of a saved propagation state: header, the pairs' canonical slots, then the device sections
+struct StateHeader {
+  char magic[8];  // "SBSESTA1"
+  int precision, N, P, L, feedback, next, n_slots_pad;
+  sbse_tdh_params params;
+};
+struct StateSection {
+  int slot;
+  size_t bytes;
+};
+std::vector<StateSection> state_sections(const sbse_ctx *ctx, int P, int L, int feedback) {
+  const size_t ng = (size_t)ctx->ng, c = ctx->precision == SBSE_FP64 ? 16 : 8;
+  std::vector<StateSection> s = {{WS_N0, (size_t)L * 8}, {WS_A0, L * ng * c}, {WS_D, (size_t)P * L * ng * c},
+                                 {WS_WACC, (size_t)P * ng * 8}};
+  if (ctx->precision != SBSE_FP64) s.push_back({WS_ACC32, (size_t)P * ng * 4});
+  if (feedback) s.push_back({WS_EM1, (size_t)P * ng * c});
+  return s;
+}
+size_t state_header_bytes(int P) { return (sizeof(StateHeader) + (size_t)P * sizeof(int) + 15) / 16 * 16; }
+}  // namespace
+
 extern "C" {
 
 int sbse_create(sbse_ctx **out, int device, int precision) {
@@ -1282,6 +1339,11 @@ int sbse_coefficients(uint64_t seed, int n_s, int n_occ, int dist, double *out) 
 
 int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int *pi, const int *pj,
                  const double *coeff, double *w_out) {
+  return sbse_apply_W_range(ctx, p, n_pairs, pi, pj, coeff, w_out, 0, p ? p->n_steps : 0);
+}
+
+int sbse_apply_W_range(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int *pi, const int *pj,
+                       const double *coeff, double *w_out, int n_begin, int n_end) {
   if (!ctx) return SBSE_ERR_INVALID_ARG;
   ctx->err.clear();
   if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
@@ -1314,11 +1376,30 @@ int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int
   } else {
     sbse_coefficients(p->seed, p->n_s, ctx->n_occ, p->coeff_dist, c.data());
   }
+  if (n_begin < 0 || n_end <= n_begin || n_end > p->n_steps)
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "need 0 <= n_begin < n_end <= n_steps");
+  auto same = [](const sbse_tdh_params &x, const sbse_tdh_params &y) {
+    return x.n_s == y.n_s && x.n_steps == y.n_steps && x.clean_every == y.clean_every && x.dt == y.dt &&
+           x.gamma == y.gamma && x.alpha == y.alpha && x.seed == y.seed && x.coeff_dist == y.coeff_dist &&
+           x.feedback == y.feedback;
+  };
+  if (n_begin > 0 && !(ctx->run.valid && ctx->run.next == n_begin && ctx->run.slots == slots &&
+                       same(ctx->run.params, *p)))
+    return fail(ctx, SBSE_ERR_NOT_READY,
+                "no propagation state of these parameters and pairs stopped at n_begin (run the range before it "
+                "or load its state)");
   CK(cudaSetDevice(ctx->device));
   ctx->have_A = false;
-  const int rc = ctx->precision == SBSE_FP64 ? run_apply_W<double>(ctx, p, slots, c)
-                                             : run_apply_W<float>(ctx, p, slots, c);
-  if (rc) return rc;
+  if (n_begin == 0) ctx->run.valid = false;
+  ctx->run.params = *p;
+  ctx->run.slots = slots;
+  const int rc = ctx->precision == SBSE_FP64 ? run_apply_W<double>(ctx, p, slots, c, n_begin, n_end)
+                                             : run_apply_W<float>(ctx, p, slots, c, n_begin, n_end);
+  if (rc) {
+    ctx->run.valid = false;
+    return rc;
+  }
+  if (n_end < p->n_steps) return SBSE_OK;  // W is stored when the last step has run
   for (int k = 0; k < n_pairs; ++k) {
     if (scan_nonfinite(ctx->W + (long long)slots[k] * ctx->ng, ctx->ng, ctx->flag, ctx->stream))
       return fail(ctx, SBSE_ERR_NUMERIC, "W has NaN or Inf (unstable propagation: reduce dt)");
@@ -1329,6 +1410,85 @@ int sbse_apply_W(sbse_ctx *ctx, const sbse_tdh_params *p, int n_pairs, const int
     for (int k = 0; k < n_pairs; ++k)
       CK(cudaMemcpy(w_out + (long long)k * ctx->ng, ctx->W + (long long)slots[k] * ctx->ng,
                     ctx->ng * sizeof(double), cudaMemcpyDeviceToHost));
+  return SBSE_OK;
+}
+
+
+int sbse_state_bytes(sbse_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ctx->run.valid) return fail(ctx, SBSE_ERR_NOT_READY, "no propagation stopped part way in this context");
+  const int P = (int)ctx->run.slots.size(), L = ctx->run.params.n_s;
+  size_t b = state_header_bytes(P);
+  for (const auto &s : state_sections(ctx, P, L, ctx->run.params.feedback)) b += s.bytes;
+  *bytes = b;
+  return SBSE_OK;
+}
+
+int sbse_save_state(sbse_ctx *ctx, void *host, size_t bytes) {
+  size_t need = 0;
+  int rc = sbse_state_bytes(ctx, &need);
+  if (rc) return rc;
+  if (!host || bytes < need) return fail(ctx, SBSE_ERR_INVALID_ARG, "state buffer missing or smaller than sbse_state_bytes");
+  const int P = (int)ctx->run.slots.size(), L = ctx->run.params.n_s;
+  StateHeader h{};
+  memcpy(h.magic, "SBSESTA1", 8);
+  h.precision = ctx->precision;
+  h.N = ctx->N;
+  h.P = P;
+  h.L = L;
+  h.feedback = ctx->run.params.feedback;
+  h.next = ctx->run.next;
+  h.params = ctx->run.params;
+  uint8_t *o = static_cast<uint8_t *>(host);
+  memcpy(o, &h, sizeof h);
+  memcpy(o + sizeof h, ctx->run.slots.data(), (size_t)P * sizeof(int));
+  size_t off = state_header_bytes(P);
+  CK(cudaSetDevice(ctx->device));
+  for (const auto &s : state_sections(ctx, P, L, h.feedback)) {
+    CK(cudaMemcpyAsync(o + off, ctx->ws[s.slot].p, s.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    off += s.bytes;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBSE_OK;
+}
+
+int sbse_load_state(sbse_ctx *ctx, const void *host, size_t bytes) {
+  if (!ctx) return SBSE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->n_states == 0) return fail(ctx, SBSE_ERR_NOT_READY, "call sbse_set_orbitals first");
+  StateHeader h{};
+  if (!host || bytes < sizeof h) return fail(ctx, SBSE_ERR_INVALID_ARG, "state buffer missing or too small");
+  const uint8_t *in = static_cast<const uint8_t *>(host);
+  memcpy(&h, in, sizeof h);
+  if (memcmp(h.magic, "SBSESTA1", 8) != 0) return fail(ctx, SBSE_ERR_INVALID_ARG, "not a saved propagation state");
+  if (h.precision != ctx->precision || h.N != ctx->N)
+    return fail(ctx, SBSE_ERR_SHAPE, "state saved on another grid or in another precision mode");
+  const int P_all = ctx->n_o * (ctx->n_o + 1) / 2;
+  if (h.P < 1 || h.P > P_all || h.L < 1 || h.L > 64 || h.next < 1 || h.next >= h.params.n_steps)
+    return fail(ctx, SBSE_ERR_INVALID_ARG, "state header out of range for this context");
+  size_t need = state_header_bytes(h.P);
+  const auto secs = state_sections(ctx, h.P, h.L, h.feedback);
+  for (const auto &s : secs) need += s.bytes;
+  if (bytes < need) return fail(ctx, SBSE_ERR_INVALID_ARG, "state buffer shorter than its header says");
+  std::vector<int> slots(h.P);
+  memcpy(slots.data(), in + sizeof h, (size_t)h.P * sizeof(int));
+  for (int s : slots)
+    if (s < 0 || s >= P_all) return fail(ctx, SBSE_ERR_INVALID_ARG, "state holds a pair outside the window");
+  CK(cudaSetDevice(ctx->device));
+  size_t off = state_header_bytes(h.P);
+  for (const auto &s : secs) {
+    void *vp;
+    int rc;
+    if ((rc = ensure(ctx, s.slot, s.bytes, &vp))) return rc;
+    CK(cudaMemcpyAsync(vp, in + off, s.bytes, cudaMemcpyHostToDevice, ctx->stream));
+    off += s.bytes;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->run.valid = true;
+  ctx->run.next = h.next;
+  ctx->run.params = h.params;
+  ctx->run.slots = slots;
   return SBSE_OK;
 }
 
@@ -1918,6 +2078,27 @@ int sbse_set_option(sbse_ctx *ctx, int option, int value) {
       return SBSE_OK;
   }
   return fail(ctx, SBSE_ERR_INVALID_ARG, "unknown option");
+}
+
+int sbse_debug_bounds(int *enabled, unsigned long long *first_fault) {
+  if (!enabled || !first_fault) return SBSE_ERR_INVALID_ARG;
+#ifdef SBSE_DEBUG_BOUNDS
+  *enabled = 1;
+#else
+  *enabled = 0;
+#endif
+  *first_fault = 0;
+  int n = 0;
+  for (auto rd : sbse::bounds_readers()) {
+    unsigned long long v = 0;
+    const int r = rd(&v);
+    if (r < 0) return SBSE_ERR_CUDA;
+    if (r > 0) {
+      if (!*first_fault) *first_fault = v;
+      ++n;
+    }
+  }
+  return n > 0 ? SBSE_ERR_NUMERIC : SBSE_OK;
 }
 
 int sbse_kernel_launches(long long *count) {

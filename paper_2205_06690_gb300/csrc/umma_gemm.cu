@@ -17,6 +17,7 @@
 
 #include <mutex>
 
+#include "bounds.cuh"
 #include "kernels.h"
 #include "tma.cuh"
 
@@ -152,6 +153,7 @@ __device__ __forceinline__ void load_unit(int u, int units_a, const float *F, co
     const int m = m0 + row;
     if (m < M) {
       const int2 q = xi[m];
+      (void)SBSE_IDX(kb, ng);
       const float *f1 = F + (long long)q.x * ng + kb, *f2 = F + (long long)q.y * ng + kb;
       if (full) {
         const float4 a0 = *reinterpret_cast<const float4 *>(f1), a1 = *reinterpret_cast<const float4 *>(f1 + 4);
@@ -378,8 +380,11 @@ __global__ void __launch_bounds__(kUmThreads)
   __shared__ uint32_t tmem_slot;
   uint8_t *a_hi = smem, *a_lo = a_hi + kUmM * kUmBK * 2;
   uint8_t *b_hi = a_lo + kUmM * kUmBK * 2, *b_lo = b_hi + kCuN * kUmBK * 2;
-  const int m0 = blockIdx.y * kUmM;
-  const long long r0 = (long long)blockIdx.x * kCuN;
+  // row tile fastest: the CTAs that read one tile of phi operands run together (L2 reuse)
+  const int mt = blockIdx.x;
+  const long long tile = blockIdx.y;
+  const int m0 = mt * kUmM;
+  const long long r0 = tile * kCuN;
   const int n_cols = M / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -402,8 +407,10 @@ __global__ void __launch_bounds__(kUmThreads)
     // the previous chunk's MMAs have completed (waited below), so its operand tiles can be replaced
     if (threadIdx.x == 0) {
       tma_bar_expect(&tbar, kCanA + kCanB);
-      tma_load_1d(a_hi, o_can + ((size_t)blockIdx.y * n_kc + it) * kCanA, kCanA, &tbar);
-      tma_load_1d(b_hi, phi_can + ((size_t)blockIdx.x * n_kc + it) * kCanB, kCanB, &tbar);
+      (void)SBSE_IDX((long long)mt * n_kc + it, (long long)gridDim.x * n_kc);
+      (void)SBSE_IDX(tile * n_kc + it, (long long)((ng + kCuN - 1) / kCuN) * n_kc);
+      tma_load_1d(a_hi, o_can + ((size_t)mt * n_kc + it) * kCanA, kCanA, &tbar);
+      tma_load_1d(b_hi, phi_can + ((size_t)tile * n_kc + it) * kCanB, kCanB, &tbar);
     }
     tma_pending = true;
     if (!__syncthreads_and(tma_bar_wait(&tbar, (unsigned)(it & 1)))) {
@@ -516,8 +523,8 @@ __global__ void __launch_bounds__(kUmThreads)
   for (int cl = threadIdx.x; cl < kUmM / 2; cl += blockDim.x) {
     const int c = c0 + cl;
     if (ok && c < n_cols) {
-      npart[((long long)blockIdx.x * n_cols + c) * 2 + 0] = (double)colsum[cl][0];
-      npart[((long long)blockIdx.x * n_cols + c) * 2 + 1] = (double)colsum[cl][1];
+      npart[(tile * n_cols + c) * 2 + 0] = (double)colsum[cl][0];
+      npart[(tile * n_cols + c) * 2 + 1] = (double)colsum[cl][1];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -555,7 +562,7 @@ void launch_umma_clean_update(const double *ov, int n_cols, const uint8_t *phi_c
       SrcRowsF64{ov, M, n_occ}, m_tiles, kchunks(n_occ), o_can);
   const size_t smem = (size_t)kCanA + kCanB;
   raise_smem_limit((const void *)k_umma_clean_update, smem);
-  dim3 grid((unsigned)umma_clean_update_tiles(ng), (unsigned)m_tiles);
+  dim3 grid((unsigned)m_tiles, (unsigned)umma_clean_update_tiles(ng));
   k_umma_clean_update<<<grid, kUmThreads, smem, s>>>(o_can, M, phi_can, kchunks(n_occ), ng, d_interleaved,
                                                      a_interleaved, L, npart, err);
   count_launch(2);
@@ -767,6 +774,9 @@ __global__ void __launch_bounds__(kOvThreads, 1)
         break;
       }
       const long long k0 = kbeg + (long long)it * kOvKS;
+      (void)SBSE_IDX(k0, ng);
+      (void)SBSE_IDX(c0, n_cols);
+      (void)SBSE_IDX(k0 / kOvKS, (ng + kOvKS - 1) / kOvKS);
       if (lane == 0) {
         // d viewed as n_cols rows of 2 ng floats: boxes of 64 rows x 32 floats at float x = 2 k0
         // (+ 32), a multiple of 64 (16-byte rule); rows past n_cols and points past ng read as zero
@@ -928,6 +938,23 @@ static EncodeTiledFn encode_tiled() {
   return fn;
 }
 
+bool make_tensor_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                         const uint64_t *strides_bytes, const uint32_t *box, bool swizzle128) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || rank < 1 || rank > 5) return false;
+  cuuint64_t d[5], st[4];
+  cuuint32_t b[5], e[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    e[i] = 1;
+    if (i + 1 < rank) st[i] = strides_bytes[i];
+  }
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base), d, st, b, e,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool umma_clean_ov_supported(int n_occ, long long ng) {
   const int nb = ov_rows(n_occ);
   // rows of 2 ng floats: a 16-byte multiple stride; 2 ng < 2^32 for the tensor-copy coordinates
@@ -949,17 +976,11 @@ int launch_umma_clean_ov(const float *d_interleaved, int n_cols, const uint8_t *
   long long kc, chunks;
   ov_grid(n_cols, ng, &mt, &kc, &chunks);
   const size_t smem = (size_t)S * ov_stage_bytes(nb) + kOvAlign;
-  EncodeTiledFn enc = encode_tiled();
-  if (!enc) return -1;
   CUtensorMap dmap;
-  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ng), (cuuint64_t)n_cols};
-  const cuuint64_t strides[1] = {(cuuint64_t)(2 * ng * sizeof(float))};
-  const cuuint32_t box[2] = {32u, (cuuint32_t)kOvCols};
-  const cuuint32_t estr[2] = {1u, 1u};
-  if (enc(&dmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d_interleaved, dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return -1;
+  const uint64_t dims[2] = {(uint64_t)(2 * ng), (uint64_t)n_cols};
+  const uint64_t strides[1] = {(uint64_t)(2 * ng * sizeof(float))};
+  const uint32_t box[2] = {32u, (uint32_t)kOvCols};
+  if (!make_tensor_map_f32(&dmap, d_interleaved, 2, dims, strides, box, true)) return -1;
   raise_smem_limit((const void *)k_umma_clean_ov, smem);
   dim3 grid((unsigned)mt, (unsigned)chunks);
   k_umma_clean_ov<<<grid, kOvThreads, smem, s>>>(dmap, n_cols, phi_t, nb, n_occ, ng, kc, S, work, err);

@@ -162,20 +162,22 @@ def train_schedule(net: B.FNO, x, t, epochs: int, batch: int, lr0: float, lr1: f
 
 
 def surrogate_pol_apply_W(ctx, net: B.FNO, scales: Scales, params: B.TDHParams, pairs, n_sys: int,
-                          spot_frac: float = 0.05, tol: float = 0.5, seed: int = 0,
-                          max_fail_frac: float = 0.5):
+                          spot_frac: float = 0.05, tol: float = 1.0, seed: int = 0,
+                          max_fail_frac: float = 0.5, seed_step: int = 7919):
     """W_ij = q_ij + surrogate W^pol_ij for all pairs, then a spot check of a random `spot_frac` of
-    them (at least one) against fresh propagation, whose W replaces the surrogate's; if more than
-    `max_fail_frac` of the spot checks miss by more than `tol` (relative error of the polarisation
-    part), every other pair is propagated as well. Returns a report dict."""
+    them (at least one) against fresh propagation. The stochastic W^pol of one propagation carries
+    sampling noise, so a spot pair is propagated with two stochastic seeds (params.seed and
+    params.seed + seed_step) and the surrogate passes when it is no farther from the first sample
+    than the second sample is: ||sur - t1|| <= tol ||t2 - t1||. The spot pairs keep the mean of the
+    two samples; if more than `max_fail_frac` of the spot checks fail, every other pair is
+    propagated as well (the method-level fallback). Returns a report dict."""
     torch = _torch()
     n_net = net.n
     t0 = time.perf_counter()
     B.sbse_bare_W(ctx.h, pairs)
     rng = np.random.default_rng(seed)
-    n_spot = max(1, int(round(spot_frac * len(pairs))))
+    n_spot = 0 if spot_frac <= 0 else max(1, int(round(spot_frac * len(pairs))))  # 0: no spot check
     spot = [pairs[k] for k in sorted(rng.choice(len(pairs), size=n_spot, replace=False))]
-    q_spot = B.sbse_get_W(ctx.h, spot, n_sys ** 3)
     bmax = net.max_batch
     y = torch.empty((bmax, n_net ** 3), dtype=torch.float32, device="cuda")
     ys = y if n_sys == n_net else torch.empty((bmax, n_sys ** 3), dtype=torch.float32, device="cuda")
@@ -188,12 +190,16 @@ def surrogate_pol_apply_W(ctx, net: B.FNO, scales: Scales, params: B.TDHParams, 
         B.sbse_add_W(ctx.h, chunk, ys.data_ptr(), scales.s_w)
     torch.cuda.synchronize()
     t_sur = time.perf_counter() - t0
-    w_sur = B.sbse_get_W(ctx.h, spot, n_sys ** 3)
     t1 = time.perf_counter()
-    w_tdh = ctx.apply_W(params, spot, copy_out=True)  # propagated W replaces the spot pairs
+    ratio = np.zeros(0)
+    if spot:
+        w_sur = B.sbse_get_W(ctx.h, spot, n_sys ** 3)
+        w1 = ctx.apply_W(params, spot, copy_out=True)
+        w2 = ctx.apply_W(dataclasses.replace(params, seed=params.seed + seed_step), spot, copy_out=True)
+        B.sbse_set_W(ctx.h, spot, 0.5 * (w1 + w2))
+        ratio = np.linalg.norm(w_sur - w1, axis=1) / np.linalg.norm(w2 - w1, axis=1)
     t_tdh = time.perf_counter() - t1
-    err = np.linalg.norm(w_sur - w_tdh, axis=1) / np.linalg.norm(w_tdh - q_spot, axis=1)
-    failed = [p for p, e in zip(spot, err) if e > tol]
+    failed = [p for p, e in zip(spot, ratio) if e > tol]
     fallback = len(failed) > max_fail_frac * n_spot
     t_fb = 0.0
     if fallback:
@@ -202,6 +208,6 @@ def surrogate_pol_apply_W(ctx, net: B.FNO, scales: Scales, params: B.TDHParams, 
             t2 = time.perf_counter()
             ctx.apply_W(params, rest)
             t_fb = time.perf_counter() - t2
-    return {"spot_pairs": spot, "spot_rel_err_pol": err.tolist(), "failed": failed, "fallback": fallback,
+    return {"spot_pairs": spot, "spot_ratio": ratio.tolist(), "failed": failed, "fallback": fallback,
             "surrogate_s": t_sur, "spot_tdh_s": t_tdh, "fallback_s": t_fb,
-            "surrogate_s_per_pair": t_sur / len(pairs), "tdh_s_per_pair": t_tdh / len(spot)}
+            "surrogate_s_per_pair": t_sur / len(pairs), "tdh_s_per_pair": t_tdh / max(1, 2 * len(spot))}

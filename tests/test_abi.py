@@ -64,3 +64,12 @@ def test_header_is_plain_c(tmp_path):
         r = subprocess.run([cc, *lang, "-Wall", "-Werror", "-I", os.path.join(root, "include"), "-c", str(src),
                             "-o", str(tmp_path / "use.o")], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_release_build_has_no_debug_bounds_checks():
+    """The release library reports that it carries no device-side bounds checks (the call needs no
+    GPU: the release build registers no records to read)."""
+    from paper_2205_06690_gb300 import binding as B
+    if B.LIB_PATH.endswith("libsbse_dbg.so"):
+        pytest.skip("the debug build is loaded")
+    assert B.sbse_debug_bounds() == (False, 0)

@@ -3,6 +3,8 @@
 The CUDA kernels use BF16 copies of the spectral and pointwise weights and FP32 sums; the oracle is
 given the same BF16-rounded weights, so the remaining differences are FP32 rounding (relative
 1e-4 on outputs, 2e-3 on gradients, which sum O(B N^3) FP32 terms)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -276,14 +278,17 @@ def test_polarisation_surrogate_on_a_coarser_network_grid():
         e0, _ = held_out_err()
         hist = S.train_schedule(net, x, t, epochs=40, batch=4, lr0=3e-3, lr1=1e-4)
         e1, pol = held_out_err()
+        pol_b = S.polarisation_targets(c, dataclasses.replace(prm, seed=prm.seed + 7919), pairs, N, N)
+        pol_mean = 0.5 * (pol_ref + pol_b.cpu().numpy().astype(np.float64))
         Bd.sbse_bare_W(c.h, pairs)
         q = Bd.sbse_get_W(c.h, pairs, N ** 3)
-        rep = S.surrogate_pol_apply_W(c, net, sc, prm, pairs, N, spot_frac=0.2, tol=10.0, seed=2)
+        rep = S.surrogate_pol_apply_W(c, net, sc, prm, pairs, N, spot_frac=0.2, tol=100.0, seed=2)
         w = Bd.sbse_get_W(c.h, pairs, N ** 3)
         spot = set(rep["spot_pairs"])
+        assert len(spot) == 2 and len(rep["spot_ratio"]) == 2
         for k, pr in enumerate(pairs):
-            if pr in spot:  # the propagated W (same seed and parameters as pol_ref)
-                assert rel_err(w[k] - q[k], pol_ref[k]) < 1e-3
+            if pr in spot:  # the mean of the two propagated samples (same seeds and parameters)
+                assert rel_err(w[k] - q[k], pol_mean[k]) < 1e-3
             else:  # q + the resampled prediction
                 assert rel_err(w[k] - q[k], pol[k]) < 1e-5
         assert not rep["fallback"]

@@ -33,8 +33,9 @@ def _system(N):
     return _SYS[N]
 
 
-def _run(B, s, precision, prm, pairs, n_occ=6, n_o=3, n_c=4):
+def _run(B, s, precision, prm, pairs, n_occ=6, n_o=3, n_c=4, tma=1):
     with B.Context(0, precision) as c:
+        B.sbse_set_option(c.h, B.SBSE_OPT_TMA_PLANES, tma)
         c.set_grid(s.N, s.box, s.v_loc)
         c.set_orbitals(n_occ, n_o, n_c, s.phi[:n_occ + n_c], s.eps[:n_occ + n_c], 0.5)
         return c.apply_W(prm, pairs, copy_out=True)
@@ -53,6 +54,10 @@ def test_split_grids_match_oracle(B, N, M, dist, fb):
     pairs = [(0, 0), (0, 2), (1, 2)]  # odd count: the last Poisson slot packs one density
     W64 = _run(B, s, B.SBSE_FP64, prm, pairs)
     W32 = _run(B, s, B.SBSE_MIXED, prm, pairs)
+    # the z sweep with its columns staged by bulk tensor copies (default) or loaded by the threads:
+    # the same arithmetic, the same result
+    W32r = _run(B, s, B.SBSE_MIXED, prm, pairs, tma=0)
+    assert np.array_equal(W32, W32r)
     coeff = tdh.stochastic_coefficients(prm.seed, prm.n_s, 6, "sign" if dist else "gaussian")
     op = tdh.TDHParams(n_steps=prm.n_steps, dt=prm.dt, gamma=prm.gamma, alpha=prm.alpha,
                        clean_every=M, feedback=bool(fb))
