@@ -6,7 +6,7 @@ N_occ = 260 (520 electrons), n_o = 16, n_c = 32 (136 pairs, A is 512 x 512), L =
 orbitals, 2000 steps of dt = 0.05, gamma = 0.1, cleaning every M = 10 steps.
 
 One step = W_ij for one block of pairs by stochastic TDH (all time steps, cleaning, damped time
-integral; the blocks of 17 pairs are taken in turn, so eight steps renew all 136), then the
+integral; the blocks of 68 pairs are taken in turn, so two steps renew all 136), then the
 exchange and direct contractions over all pairs' W, the FP64 Tamm-Dancoff matrix A and its lowest
 excitons. The whole system is also run end to end through the C ABI from pinned host buffers.
 Smaller workloads (--workload mid48 / tiny16) advance all their pairs in every step.
@@ -251,10 +251,11 @@ def measured_peaks():
 
 
 def block_default(pre) -> int:
-    """Pairs per benchmark step: every pair for the small workloads; one eighth of the 136 pairs of
-    the 96^3 system (17), so that one step (17 pairs x 2000 TDH steps + A + excitons) takes seconds
-    and eight steps refresh all of W."""
-    return pre.n_pairs if pre.n_pairs <= 64 else -(-pre.n_pairs // 8)
+    """Pairs per benchmark step: every pair for the small workloads; half of the 136 pairs of the
+    96^3 system (68), so that one step (68 pairs x 2000 TDH steps + A + excitons) takes about 14 s
+    and two steps refresh all of W. (Larger blocks amortise the per-step eta0 set and A build:
+    measured 3.9 / 4.6 / 4.8 W/s for blocks of 17 / 34 / 68 pairs.)"""
+    return pre.n_pairs if pre.n_pairs <= 64 else -(-pre.n_pairs // 2)
 
 
 def batch_bench(args):
