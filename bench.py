@@ -225,7 +225,7 @@ def kernel_source_hash(workload: str = "default") -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(phase, workload, mixed):
+def profiled_traffic(phase, workload, mixed, sweep_bytes=None):
     """DRAM bytes (read + write) per launch of the pass, from the committed ncu summary, when it
     was taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", f"pair_passes_{workload}_traffic.txt")
@@ -236,7 +236,15 @@ def profiled_traffic(phase, workload, mixed):
     if d.get("source_sha256_16") != kernel_source_hash(workload):
         return None, "kernel sources changed since the ncu capture"
     v = d.get("dram_bytes_per_launch", {}).get(str(phase))
-    return (float(v), os.path.relpath(path, ROOT)) if v else (None, None)
+    if not v:
+        return None, None
+    note = os.path.relpath(path, ROOT)
+    alg = d.get("algorithmic_bytes_per_launch")
+    if sweep_bytes and alg and abs(sweep_bytes - alg) > 1e-6 * alg:
+        # another block size than the capture's: these passes move their bytes per orbital
+        v = float(v) * sweep_bytes / alg
+        note += f" (scaled from its {alg / 1e9:.3f} GB launch to this {sweep_bytes / 1e9:.3f} GB one)"
+    return float(v), note
 
 
 def measured_peaks():
@@ -767,7 +775,8 @@ def main():
     split = pre.N in (80, 96)
     if split:  # two sweeps per step: the kinetic propagator as three one-dimensional operators
         pass_names = {5: "plane kinetic pass k_plane_kin2 (potential phase + x, y kinetic operators)",
-                      7: "z kinetic pass k_zkin2 (z kinetic operator + induced density)"}
+                      7: "z kinetic pass k_zkin2_tma (z kinetic operator + induced density; columns "
+                         "staged by tensor copies)"}
     else:
         pass_names = {5: "forward plane pass k_plane_fwd (potential phase + x, y FFTs)",
                       6: "z-column pass k_zcol_tma (z FFT, kinetic phase, inverse z FFT)",
@@ -780,7 +789,7 @@ def main():
             passes[str(ph)] = {"kernel": name, "avg_us": 1e3 * t / nl, "launches": nl,
                                "achieved": gbs, "frac": gbs / peak, "share_of_step": t / ms_prof}
     dom = max(passes, key=lambda k: passes[k]["share_of_step"]) if passes else None
-    traffic, traffic_note = profiled_traffic(dom and int(dom), pre.name, prec == B.SBSE_MIXED)
+    traffic, traffic_note = profiled_traffic(dom and int(dom), pre.name, prec == B.SBSE_MIXED, sweep_bytes)
     ms0, n0 = phase[0]
     step_gbs = (sweep_bytes + pre.n_s * pre.N ** 3 * 2 * csize) / (ms0 / n0 / 1e3) / 1e9 if n0 else None
     prof_note = (f"{prof_steps} further benchmark steps with CUDA events around every pass on the "
