@@ -731,11 +731,32 @@ def main():
         torch.cuda.synchronize()
         ms32 = f0.elapsed_time(f1) * n_steps / short
         ctx.apply_W(prm, blocks[0])  # restore the block's full-length W
+        # full-length exciton check of the mixed path against the FP64 path: the same system,
+        # stochastic set and step count on the valence window cut to n_o = 3 (6 pairs, A of
+        # 3 n_c rows; the FP64 run of every pair would take about 20 min)
+        n_ow = min(3, pre.n_o)
+        pairs_w = [(i, j) for i in range(n_ow) for j in range(i, n_ow)]
+        exc = {}
+        t_chk = time.perf_counter()
+        for pm in (B.SBSE_FP64, B.SBSE_MIXED):
+            with B.Context(local, pm) as cw:
+                cw.set_grid(pre.N, pre.box, system.v_loc)
+                cw.set_orbitals(pre.n_occ, n_ow, pre.n_c, phi, eps, pre.scissor)
+                cw.apply_W(prm, pairs_w)
+                cw.build_A(copy_out=False)
+                exc[pm] = cw.spectrum(min(pre.n_exc, n_ow * pre.n_c))
+        dev_mev = np.abs(exc[B.SBSE_MIXED] - exc[B.SBSE_FP64]) * 27211.386245988
+        exciton_check = {"window": f"n_o = {n_ow} ({len(pairs_w)} pairs), n_c = {pre.n_c}, all {n_steps} TDH "
+                                   f"steps, seed {prm.seed}",
+                         "lowest": len(dev_mev), "max_dev_mev": float(dev_mev.max()),
+                         "dev_mev": [float(x) for x in dev_mev], "target_mev": 5.0,
+                         "seconds": time.perf_counter() - t_chk}
         fp64 = {"value": len(blocks[0]) / (ms64 / 1e3), "unit": "W-applications/s",
                 "sample": f"{len(blocks[0])} pairs x {short} TDH steps, scaled to {n_steps}",
                 "mixed_same_sample": len(blocks[0]) / (ms32 / 1e3),
                 "mixed_speedup": ms64 / ms32,
-                "a_build_ms": a64_ms, "a_build_speedup_mixed": a64_ms / a_build_ms}
+                "a_build_ms": a64_ms, "a_build_speedup_mixed": a64_ms / a_build_ms,
+                "exciton_check_mixed_vs_fp64": exciton_check}
 
     # learned form: FNO surrogate of the workload's shape (64^3, width 32, 12 modes, 4 layers)
     surrogate = None

@@ -1,7 +1,7 @@
 """The paper-scale workload itself (Sec. III: 520 electrons on ~0.85M grid points; here 96^3, 170
 Gaussian wells, N_occ = 260, n_o = 16, n_c = 32, L = 10), GPU only.
 
-* In the launch configuration that bench.py times (one block of 17 of the 136 pairs per call, all
+* In the launch configuration that bench.py times (one block of 68 of the 136 pairs per call, all
   L = 10 stochastic orbitals, cleaning every 10 steps against all 260 occupied states), shortened
   to 12 steps: W of a sampled pair of the block against the FP64 oracle (FP64 mode 1e-10, mixed
   mode 2e-3), and the mixed block against the FP64 block.
@@ -47,13 +47,13 @@ def _ctx(B, s, precision, n_o=16):
 def test_large96_block_launch_sampled_pair_vs_oracle(B, large96):
     s = large96
     p = s.preset
-    pairs = tdh.pair_list(p.n_o)[:17]
+    pairs = tdh.pair_list(p.n_o)[:68]
     prm = B.TDHParams(n_s=10, n_steps=12, clean_every=10, dt=p.dt, gamma=p.gamma, alpha=p.alpha, seed=2)
     with _ctx(B, s, B.SBSE_FP64) as c:
         W64 = c.apply_W(prm, pairs, copy_out=True)
     with _ctx(B, s, B.SBSE_MIXED) as c:
         W32 = c.apply_W(prm, pairs, copy_out=True)
-    k = 13
+    k = 53
     i, j = pairs[k]
     g = tdh.Grid(s.N, s.box)
     coeff = tdh.stochastic_coefficients(2, 10, p.n_occ, "gaussian")
