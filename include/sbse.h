@@ -266,8 +266,9 @@ int sbse_set_scissor(sbse_ctx *ctx, double scissor);
  * loaded on a device, which under CUDA's default lazy loading is the first call there: a caller
  * whose memory pool will take the whole GPU should make one call (or set
  * CUDA_MODULE_LOADING=EAGER) before the pool reserves it, else that first call can fail with CUDA.
- * Make that first call before any stream capture. Every call synchronises `stream` before it
- * returns. All calls on a device share the array, so calls that overlap on the GPU race; the
+ * Every call synchronises `stream` before it returns, so it must not be called on a stream that is
+ * being captured into a graph (the synchronisation would end the capture). All calls on a device
+ * share the array, so calls that overlap on the GPU race; the
  * array keeps the last call's contents, and nothing in it needs to start at zero.
  * Errors: INVALID_ARG (null pointer, k outside 1..n), SHAPE (n > SBSE_NOALLOC_MAX_N), CUDA;
  * the message is available from sbse_last_error(NULL). */

@@ -332,8 +332,16 @@ __global__ void __launch_bounds__(kPgThreads)
 // from d in place (coalesced through shared memory) and writes per-tile partial sums of
 // 2 Re(conj(eta0) d) and |d|^2 per column for the renormalisation.
 constexpr int kCuN = 256;
-constexpr unsigned kCanA = 2u * kUmM * kUmBK * 2;  // bytes of one A chunk (hi, lo)
-constexpr unsigned kCanB = 2u * kCuN * kUmBK * 2;  // bytes of one B chunk (hi, lo)
+constexpr int kUdBK = 32;                          // occupied states per operand chunk of the update
+constexpr int kUdStages = 2;                       // operand chunks in flight per CTA
+constexpr unsigned kCanA = 2u * kUmM * kUdBK * 2;  // bytes of one A chunk (hi, lo): 16 KB
+constexpr unsigned kCanB = 2u * kCuN * kUdBK * 2;  // bytes of one B chunk (hi, lo): 32 KB
+
+// offset of element (row, core matrix kc) of an R x kUdBK BF16 tile, canonical K-major, no swizzle:
+// K-adjacent core matrices 128 B apart, 8-row groups kUdBK / 8 x 128 B apart
+__device__ __forceinline__ uint32_t canon_ud_off(int row, int kc) {
+  return (uint32_t)(((row >> 3) * (kUdBK / 8) + kc) * 128 + (row & 7) * 16);
+}
 
 // canonical BF16 hi / lo tiles: out[tile][chunk] = hi (R x 64) then lo (R x 64); element (row, k)
 // of a tile is src(tile R + row, chunk 64 + k), zero outside the source. Thread per (row, group of
@@ -354,7 +362,8 @@ struct SrcColsF32 {  // phi^T: element (r, s) = phi[s][r]
 template <int R, class Src>
 __global__ void k_canon_tiles(Src src, long long n_tiles, int n_kc, uint8_t *out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long per_chunk = (long long)R * 8, per_tile = per_chunk * n_kc;
+  constexpr int G = kUdBK / 8;  // groups of 8 K values per chunk
+  const long long per_chunk = (long long)R * G, per_tile = per_chunk * n_kc;
   if (t >= n_tiles * per_tile) return;
   const long long tile = t / per_tile;
   const long long rem = t - tile * per_tile;
@@ -363,23 +372,24 @@ __global__ void k_canon_tiles(Src src, long long n_tiles, int n_kc, uint8_t *out
   const int g = rem2 / R, row = rem2 - g * R;
   float x[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) x[j] = src(tile * R + row, kc * kUmBK + g * 8 + j);
+  for (int j = 0; j < 8; ++j) x[j] = src(tile * R + row, kc * kUdBK + g * 8 + j);
   uint4 hi, lo;
   split8(x, &hi, &lo);
-  uint8_t *base = out + (tile * n_kc + kc) * (2ll * R * kUmBK * 2);
-  const uint32_t off = canon_off(row, g);
+  uint8_t *base = out + (tile * n_kc + kc) * (2ll * R * kUdBK * 2);
+  const uint32_t off = canon_ud_off(row, g);
   *reinterpret_cast<uint4 *>(base + off) = hi;
-  *reinterpret_cast<uint4 *>(base + (size_t)R * kUmBK * 2 + off) = lo;
+  *reinterpret_cast<uint4 *>(base + (size_t)R * kUdBK * 2 + off) = lo;
 }
 
 __global__ void __launch_bounds__(kUmThreads)
     k_umma_clean_update(const uint8_t *o_can, int M, const uint8_t *phi_can, int n_kc, long long ng, float *d,
                         const float *a, int L, double *npart, int *err) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar, tbar;
+  __shared__ __align__(8) uint64_t full[kUdStages], done[kUdStages];
   __shared__ uint32_t tmem_slot;
-  uint8_t *a_hi = smem, *a_lo = a_hi + kUmM * kUmBK * 2;
-  uint8_t *b_hi = a_lo + kUmM * kUmBK * 2, *b_lo = b_hi + kCuN * kUmBK * 2;
+  __shared__ int fail;
+  // stage s: A chunk (hi, lo) then B chunk (hi, lo), as laid out by k_canon_tiles
+  auto stage = [&](int s) { return smem + (size_t)s * (kCanA + kCanB); };
   // row tile fastest: the CTAs that read one tile of phi operands run together (L2 reuse)
   const int mt = blockIdx.x;
   const long long tile = blockIdx.y;
@@ -393,57 +403,74 @@ __global__ void __launch_bounds__(kUmThreads)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    tma_bar_init(&tbar, 1);
+    for (int s = 0; s < kUdStages; ++s) {
+      tma_bar_init(&full[s], 1);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done[s])));
+    }
+    fail = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = make_idesc(kUmM, kCuN);
-  bool ok = true, tma_pending = false;
-  int mma_issued = 0;
-  for (int it = 0; it < n_kc; ++it) {
-    // the previous chunk's MMAs have completed (waited below), so its operand tiles can be replaced
-    if (threadIdx.x == 0) {
-      tma_bar_expect(&tbar, kCanA + kCanB);
+  if (threadIdx.x == 0) {
+    // One thread drives a ring of kUdStages operand chunks: the copies of chunk it + kUdStages are
+    // issued as soon as the MMAs of chunk it have read its stage, so copies and MMAs overlap.
+    auto load = [&](int it) {
+      const int s = it % kUdStages;
       (void)SBSE_IDX((long long)mt * n_kc + it, (long long)gridDim.x * n_kc);
       (void)SBSE_IDX(tile * n_kc + it, (long long)((ng + kCuN - 1) / kCuN) * n_kc);
-      tma_load_1d(a_hi, o_can + ((size_t)mt * n_kc + it) * kCanA, kCanA, &tbar);
-      tma_load_1d(b_hi, phi_can + ((size_t)tile * n_kc + it) * kCanB, kCanB, &tbar);
-    }
-    tma_pending = true;
-    if (!__syncthreads_and(tma_bar_wait(&tbar, (unsigned)(it & 1)))) {
-      ok = false;
-      break;
-    }
-    tma_pending = false;
-    if (threadIdx.x == 0) {
+      tma_bar_expect(&full[s], kCanA + kCanB);
+      tma_load_1d(stage(s), o_can + ((size_t)mt * n_kc + it) * kCanA, kCanA, &full[s]);
+      tma_load_1d(stage(s) + kCanA, phi_can + ((size_t)tile * n_kc + it) * kCanB, kCanB, &full[s]);
+    };
+    int loaded = 0, committed = 0;
+    for (; loaded < n_kc && loaded < kUdStages; ++loaded) load(loaded);
+    bool ok = true;
+    for (int it = 0; it < n_kc && ok; ++it) {
+      const int s = it % kUdStages;
+      if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / kUdStages) & 1))) {
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+      const uint32_t ah = smem_u32(stage(s)), al = ah + kUmM * kUdBK * 2;
+      const uint32_t bh = ah + kCanA, bl = bh + kCuN * kUdBK * 2;
 #pragma unroll
-      for (int t = 0; t < kUmBK / 16; ++t) {
-        const uint32_t o = t * 256;
-        const uint64_t dah = make_desc(ah + o, 128, 1024), dal = make_desc(al + o, 128, 1024);
-        const uint64_t dbh = make_desc(bh + o, 128, 1024), dbl = make_desc(bl + o, 128, 1024);
+      for (int t = 0; t < kUdBK / 16; ++t) {
+        const uint32_t o = t * 256;  // two core matrices (16 states) per MMA along K
+        const uint64_t dah = make_desc(ah + o, 128, kUdBK / 8 * 128), dal = make_desc(al + o, 128, kUdBK / 8 * 128);
+        const uint64_t dbh = make_desc(bh + o, 128, kUdBK / 8 * 128), dbl = make_desc(bl + o, 128, kUdBK / 8 * 128);
         mma_bf16(tmem, dah, dbh, idesc, (it > 0 || t > 0) ? 1u : 0u);
         mma_bf16(tmem, dah, dbl, idesc, 1u);
         mma_bf16(tmem, dal, dbh, idesc, 1u);
       }
-      mma_commit(smem_u32(&mbar));
+      mma_commit(smem_u32(&done[s]));
+      ++committed;
+      if (loaded < n_kc) {  // the stage is refilled once its MMAs are done with it
+        if (!mbar_wait(smem_u32(&done[s]), (uint32_t)((it / kUdStages) & 1))) {
+          ok = false;
+          break;
+        }
+        load(loaded++);
+      }
     }
-    ++mma_issued;
-    if (!__syncthreads_and(mbar_wait(smem_u32(&mbar), (uint32_t)(it & 1)))) {
-      ok = false;
-      break;
+    // every MMA done (commits complete in order: the last one covers the rest)
+    if (ok && committed > 0)
+      ok = mbar_wait(smem_u32(&done[(committed - 1) % kUdStages]), (uint32_t)(((committed - 1) / kUdStages) & 1));
+    if (!ok) {
+      fail = 1;
+      atomicExch(err, 1);
+      // copies and MMAs still in flight must land before shared and tensor memory are released
+      for (int it = committed; it < loaded; ++it)
+        mbar_wait(smem_u32(&full[it % kUdStages]), (uint32_t)((it / kUdStages) & 1));
+      if (committed > 0)
+        mbar_wait(smem_u32(&done[(committed - 1) % kUdStages]), (uint32_t)(((committed - 1) / kUdStages) & 1));
     }
   }
-  if (!ok) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
-    // copies and MMAs still in flight must finish before shared and tensor memory are released
-    if (tma_pending) tma_bar_wait(&tbar, (unsigned)((mma_issued) & 1));
-    if (mma_issued > 0) mbar_wait(smem_u32(&mbar), (uint32_t)((mma_issued - 1) & 1));
-  }
+  __syncthreads();
+  const bool ok = fail == 0;
   asm volatile("tcgen05.fence::after_thread_sync;");
   // Epilogue, in two halves of 128 grid points: the accumulator rows (m = 2c + h) are staged in the
   // (now free) operand shared memory with a padded stride, then every warp updates whole complex
@@ -535,7 +562,7 @@ __global__ void __launch_bounds__(kUmThreads)
 // grid-point tiles of the tensor-core cleaning update (rows of its norm partials)
 long long umma_clean_update_tiles(long long ng) { return (ng + kCuN - 1) / kCuN; }
 
-static int kchunks(int n_occ) { return (n_occ + kUmBK - 1) / kUmBK; }
+static int kchunks(int n_occ) { return (n_occ + kUdBK - 1) / kUdBK; }
 
 size_t umma_update_phi_bytes(long long ng, int n_occ) {
   return (size_t)umma_clean_update_tiles(ng) * kchunks(n_occ) * kCanB;
@@ -546,7 +573,7 @@ size_t umma_update_o_bytes(int n_cols, int n_occ) {
 
 void umma_prepare_update_phi(const float *phi, int n_occ, long long ng, uint8_t *phi_can, cudaStream_t s) {
   const long long tiles = umma_clean_update_tiles(ng);
-  const long long threads = tiles * kchunks(n_occ) * kCuN * 8;
+  const long long threads = tiles * kchunks(n_occ) * kCuN * (kUdBK / 8);
   k_canon_tiles<kCuN, SrcColsF32><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
       SrcColsF32{phi, ng, n_occ}, tiles, kchunks(n_occ), phi_can);
   count_launch(1);
@@ -557,10 +584,10 @@ void launch_umma_clean_update(const double *ov, int n_cols, const uint8_t *phi_c
                               uint8_t *o_can, int *err, cudaStream_t s) {
   const int M = 2 * n_cols;
   const long long m_tiles = (M + kUmM - 1) / kUmM;
-  const long long threads = m_tiles * kchunks(n_occ) * kUmM * 8;
+  const long long threads = m_tiles * kchunks(n_occ) * kUmM * (kUdBK / 8);
   k_canon_tiles<kUmM, SrcRowsF64><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
       SrcRowsF64{ov, M, n_occ}, m_tiles, kchunks(n_occ), o_can);
-  const size_t smem = (size_t)kCanA + kCanB;
+  const size_t smem = (size_t)kUdStages * (kCanA + kCanB);
   raise_smem_limit((const void *)k_umma_clean_update, smem);
   dim3 grid((unsigned)m_tiles, (unsigned)umma_clean_update_tiles(ng));
   k_umma_clean_update<<<grid, kUmThreads, smem, s>>>(o_can, M, phi_can, kchunks(n_occ), ng, d_interleaved,
