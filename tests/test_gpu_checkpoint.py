@@ -17,16 +17,18 @@ def B():
     return binding
 
 
-def _ctx(B, s, p, precision):
+def _ctx(B, s, p, precision, persistent=0):
     c = B.Context(0, precision)
+    B.sbse_set_option(c.h, B.SBSE_OPT_PERSISTENT, persistent)  # the persistent step kernel, where it exists
     c.set_grid(p.N, p.box, s.v_loc)
     c.set_orbitals(p.n_occ, p.n_o, p.n_c, s.phi, s.eps, 0.5)
     return c
 
 
-@pytest.mark.parametrize("N,precision_name,fb", [(16, "SBSE_FP64", 1), (16, "SBSE_MIXED", 1), (20, "SBSE_MIXED", 0),
-                                                 (80, "SBSE_MIXED", 1)])
-def test_split_run_with_saved_state_matches_one_run(B, N, precision_name, fb):
+@pytest.mark.parametrize("N,precision_name,fb,persistent", [(16, "SBSE_FP64", 1, 0), (16, "SBSE_MIXED", 1, 0),
+                                                            (20, "SBSE_MIXED", 0, 0), (80, "SBSE_MIXED", 1, 0),
+                                                            (32, "SBSE_MIXED", 1, 1)])
+def test_split_run_with_saved_state_matches_one_run(B, N, precision_name, fb, persistent):
     precision = getattr(B, precision_name)
     p = si.model_system.Preset(f"ck{N}", N=N, box=0.5 * N if N < 64 else 0.25 * N, n_wells=4, seed=N,
                                n_occ=6, n_o=3, n_c=2)
@@ -34,16 +36,16 @@ def test_split_run_with_saved_state_matches_one_run(B, N, precision_name, fb):
     prm = B.TDHParams(n_s=4, n_steps=37, clean_every=5, dt=0.05, gamma=0.1, alpha=1e-4, seed=9, feedback=fb)
     pairs = [(0, 1), (1, 1), (0, 2)]
     ng = N ** 3
-    with _ctx(B, s, p, precision) as c:
+    with _ctx(B, s, p, precision, persistent) as c:
         w_one = c.apply_W(prm, pairs, copy_out=True)
     # ranges ending inside a cleaning interval, on a cleaning step and at a flush boundary of the
     # FP32 time integral (16 steps)
     cuts = [0, 7, 15, 16, 30, 37]
-    with _ctx(B, s, p, precision) as c:
+    with _ctx(B, s, p, precision, persistent) as c:
         assert B.sbse_apply_W_range(c.h, prm, pairs, cuts[0], cuts[1]) is None
         B.sbse_apply_W_range(c.h, prm, pairs, cuts[1], cuts[2])
         state = B.sbse_save_state(c.h)
-    with _ctx(B, s, p, precision) as c2:  # a fresh context, as after a restart
+    with _ctx(B, s, p, precision, persistent) as c2:  # a fresh context, as after a restart
         B.sbse_load_state(c2.h, state)
         for a, b in zip(cuts[2:-2], cuts[3:-1]):
             B.sbse_apply_W_range(c2.h, prm, pairs, a, b)
