@@ -37,6 +37,11 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
+// a b + c e as fused multiply-adds (four per component), for sums of two complex products
+template <typename C> __device__ __forceinline__ C cmac2(C a, C b, C c, C e) {
+  return C{fma(a.x, b.x, fma(-a.y, b.y, fma(c.x, e.x, -c.y * e.y))),
+           fma(a.x, b.y, fma(a.y, b.x, fma(c.x, e.y, c.y * e.x)))};
+}
 template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
 // s * i * a for s = +-1
 template <typename C> __device__ __forceinline__ C cmul_si(C a, int s) {

@@ -111,7 +111,7 @@ __device__ __forceinline__ void kin_roundtrip(float2 (&v)[N / 2], int s, const f
   for (int k = 0; k < H; ++k) {
     const float2 o = shfl_pair(v[k]);
     const float2 kp = tab[k], mk = mt[k];
-    v[k] = cadd(cmul(v[k], kp), cmul(o, mk));
+    v[k] = cmac2(v[k], kp, o, mk);
   }
   fft_reg<float, H, +1, TwS>(v);
 }

@@ -89,7 +89,7 @@ template <typename T> __device__ __forceinline__ C2<T> renorm_value(C2<T> dv, C2
 template <typename T>
 __device__ __forceinline__ C2<T> pair_phase(C2<T> pv, C2<T> em1, C2<T> av, C2<T> dv) {
   const C2<T> E = C2<T>{T(1) + em1.x, em1.y};
-  return cmul(pv, cadd(cmul(em1, av), cmul(E, dv)));
+  return cmul(pv, cmac2(em1, av, E, dv));
 }
 
 template <typename T>
