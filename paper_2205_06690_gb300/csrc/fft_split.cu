@@ -28,6 +28,8 @@
 // for consecutive blocks and stay in L2 even when the whole table set does not fit there.
 #include <math.h>
 
+#include <type_traits>
+
 #include "fft_reg.cuh"
 #include "kernels.h"
 #include "bounds.cuh"
@@ -136,24 +138,34 @@ __device__ __forceinline__ void preop_plane(const GView<float> &g, const XfwdArg
   if constexpr (PAIR) {
     const C *dp = it.in + off + threadIdx.x, *ap = it.a + off + threadIdx.x, *pp = it.pv + off + threadIdx.x;
     const C *ep = it.em1 ? it.em1 + off + threadIdx.x : nullptr;
+    // the deferred renormalisation is pending only in the step after a cleaning (cm1 != 0, the same
+    // for the whole block): the other steps skip its arithmetic (d is then unchanged by it)
+    auto sweep = [&](auto renorm) {
+      constexpr bool RN = decltype(renorm)::value;
 #pragma unroll 1
-    for (int k0 = 0; k0 < KP; k0 += UB) {
-      C dv[UB], av[UB], pv[UB], ev[UB];
+      for (int k0 = 0; k0 < KP; k0 += UB) {
+        C dv[UB], av[UB], pv[UB], ev[UB];
 #pragma unroll
-      for (int k = 0; k < UB; ++k) {
-        if (k0 + k < KP) {
-          const int l = (k0 + k) * NT;
-          dv[k] = dp[l];
-          av[k] = ap[l];
-          pv[k] = pp[l];
-          ev[k] = ep ? ep[l] : C{0.f, 0.f};
+        for (int k = 0; k < UB; ++k) {
+          if (k0 + k < KP) {
+            const int l = (k0 + k) * NT;
+            dv[k] = dp[l];
+            av[k] = ap[l];
+            pv[k] = pp[l];
+            ev[k] = ep ? ep[l] : C{0.f, 0.f};
+          }
         }
-      }
 #pragma unroll
-      for (int k = 0; k < UB; ++k)
-        if (k0 + k < KP)
-          srow[2 * (k0 + k) * LD] = pair_phase<float>(pv[k], ev[k], av[k], renorm_value<float>(dv[k], av[k], it.cm1));
-    }
+        for (int k = 0; k < UB; ++k)
+          if (k0 + k < KP)
+            srow[2 * (k0 + k) * LD] =
+                pair_phase<float>(pv[k], ev[k], av[k], RN ? renorm_value<float>(dv[k], av[k], it.cm1) : dv[k]);
+      }
+    };
+    if (it.cm1 != 0.f)
+      sweep(std::true_type{});
+    else
+      sweep(std::false_type{});
   } else {
     auto run = [&](auto f) {
 #pragma unroll 1
