@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(2 * kZtCw, 5)
     k_zkin2_tma(const __grid_constant__ CUtensorMap dmap, GView<float> g, float2 *data, const float2 *a_next,
                 float *dens, int n_units, int L, int *err) {
   using C = float2;
-  constexpr int NN = N * N, H = N / 2, UB = 16;
+  constexpr int NN = N * N, H = N / 2, UB = 48;
   constexpr unsigned kStage = (unsigned)N * kZtCw * sizeof(C);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((kZtAlign - (tma_smem_addr(smem_raw) & (kZtAlign - 1))) & (kZtAlign - 1));
