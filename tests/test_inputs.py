@@ -79,3 +79,17 @@ def test_chebyshev_coarse_grid_start_matches_lobpcg():
     e2, vec = chfsi.lowest_states(N, box, v, 5, 4, tol=1e-8, device="cpu")
     assert np.max(np.abs(e1 - e2)) < 1e-9
     assert np.max(np.abs(vec.T @ vec - np.eye(5))) < 1e-12
+
+
+def test_learned_form_and_profiling_presets():
+    """The learned form's systems: 20-80 wells drawn per seed, N_occ = round(1.5 wells), the 96^3
+    system's box on a 64^3 grid; the profiling preset is the 96^3 grid and box with fewer states."""
+    import sbse_inputs as si
+    ps = si.fno_presets(40, first_seed=1000)
+    assert [p.seed for p in ps] == list(range(1000, 1040))
+    assert all(20 <= p.n_wells <= 80 and p.n_occ == round(1.5 * p.n_wells) for p in ps)
+    assert all(p.N == 64 and p.box == 24.0 and p.n_o == 8 and p.n_c == 8 for p in ps)
+    assert len({p.n_wells for p in ps}) > 10  # drawn, not fixed
+    assert si.fno_presets(3, first_seed=1000)[0] == ps[0]  # reproducible
+    big, prof = si.preset("large96"), si.preset("prof96")
+    assert (prof.N, prof.box) == (big.N, big.box) and prof.n_occ < big.n_occ
