@@ -326,9 +326,11 @@ __global__ void __launch_bounds__(kPgThreads)
 // ---- cleaning projection update on the tensor cores ------------------------------------------
 // d_c(r) -= sum_s O[c][s] phi_s(r) (Eq. 15) as D[m][r] = sum_s O[m][s] phi_s(r) with m = 2c + h the
 // real / imaginary row of column c; A = O (128 rows per tile), B = phi^T (256 grid points per tile),
-// K = the occupied states in chunks of 64. Both operands are split into BF16 high / low parts and
+// K = the occupied states in chunks of 32. Both operands are split into BF16 high / low parts and
 // laid out in the canonical K-major tiles once (B once per propagation, A once per cleaning), so a
-// CTA only issues two bulk copies (TMA) per K chunk and then the MMAs. The epilogue subtracts D
+// CTA only issues two bulk copies (TMA) per K chunk and then the MMAs; one thread keeps two chunks
+// in flight (the copies of the next chunk land while the MMAs of the current one run). The
+// epilogue subtracts D
 // from d in place (coalesced through shared memory) and writes per-tile partial sums of
 // 2 Re(conj(eta0) d) and |d|^2 per column for the renormalisation.
 constexpr int kCuN = 256;
